@@ -1,0 +1,119 @@
+"""CPU FP64 oracle for the noise-reduction step (Section V): brute-force sub-boxes and the
+literal Lanczos (windowed-sinc) resampling sum.
+
+TEST INFRASTRUCTURE ONLY -- see the package docstring.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+from . import core
+
+# ----------------------------------------------------------------------------------------------
+# method of sub-boxes (Section V A)
+# ----------------------------------------------------------------------------------------------
+
+
+def subbox_fields(model, disorder: str, mode: int) -> np.ndarray:
+    """Per-atom amplitudes whose sub-box transforms are averaged, [model][site][n1][n2][n3][ncomp]:
+    occupancy b delta (TOTAL) or b (delta - c) (DIFFUSE); moments M (TOTAL) or M - <M>
+    (DIFFUSE).  The scattering length b is applied here, the form factor by the sum."""
+    if disorder == "occ":
+        x = model.occ.astype(np.float64)
+        if mode == core.DIFFUSE:
+            x = x - core.mean_occupancy(model)[None, :, None, None, None]
+        x = x * model.scat_len[None, :, None, None, None]
+        return x[..., None]
+    if disorder == "spin":
+        M = model.spins.astype(np.float64)
+        if mode == core.DIFFUSE:
+            M = M - core.mean_moment(model)[None, :, None, None, None, :]
+        return M * model.scat_len[None, :, None, None, None, None]
+    raise ValueError(disorder)
+
+
+def subbox_intensity(model, disorder: str, mode: int, nsb: int, hkl: np.ndarray) -> np.ndarray:
+    """Every lattice point o of the periodic supercell is the origin of one sub-box of nsb^3
+    cells with open boundaries (the every-lattice-point variant of Section V A); the box holds
+    the atoms of cells o + d, d in [0, nsb)^3, at their unwrapped positions o + d + r_mu, with the
+    amplitudes of the wrapped cells (o + d) mod n.  I(Q) = sum_o |F_o(Q)|^2 / (ncell nsite nsb^3),
+    averaged over supercells (magnetic: C |F_o,perp|^2, Eqs. mag_intensity, mag_projection)."""
+    x = subbox_fields(model, disorder, mode)
+    ncomp = x.shape[-1]
+    n = np.asarray(model.cells)
+    d = np.stack(np.meshgrid(*(np.arange(nsb),) * 3, indexing="ij"), -1).reshape(-1, 3)
+    nbox_atoms = d.shape[0] * model.nsite
+    site = np.repeat(np.arange(model.nsite), d.shape[0])
+    Q = core.q_cart(hkl, model.lattice)
+    acc = np.zeros(hkl.shape[0])
+    origins = np.stack(np.meshgrid(*(np.arange(c) for c in model.cells), indexing="ij"),
+                       -1).reshape(-1, 3)
+    for m in range(model.nmodels):
+        for o in origins:
+            cells = o[None, :] + d                                   # unwrapped
+            wrapped = np.mod(cells, n)
+            frac = (cells[None, :, :] + model.sites[:, None, :]).reshape(-1, 3)
+            amp = x[m][:, wrapped[:, 0], wrapped[:, 1], wrapped[:, 2], :].reshape(nbox_atoms, ncomp)
+            F = core.structure_factor(frac, None, amp, site, model.ff_kind, model.ff_coef,
+                                      model.lattice, hkl)
+            if disorder == "spin":
+                acc += core.perp_sq(F, Q)
+            else:
+                acc += np.abs(F[:, 0]) ** 2
+    I = acc / (model.nmodels * model.ncell * model.nsite * nsb ** 3)
+    return core.C_MAG * I if disorder == "spin" else I
+
+
+# ----------------------------------------------------------------------------------------------
+# Lanczos resampling (Section V B)
+# ----------------------------------------------------------------------------------------------
+
+
+def sinc(x):
+    """sinc(x) = sin(x) / x, sinc(0) = 1 (the paper's unnormalised convention)."""
+    x = np.asarray(x, dtype=np.float64)
+    safe = np.where(x == 0.0, 1.0, x)
+    return np.where(x == 0.0, 1.0, np.sin(safe) / safe)
+
+
+def lanczos_parameters(m: int, mprime: int = 2):
+    """(r_cut, m_eff): r_cut = 0.5 (1 - 1/m) for the plain window (m' = 2), and for the variant
+    that reaches zero at 1/m', r_cut = (1 - 1/m)/m' with m replaced by m m'/2 in the window."""
+    return (1.0 - 1.0 / m) / mprime, m * mprime / 2.0
+
+
+def lanczos_weight(dQ: np.ndarray, m: int, mprime: int = 2) -> np.ndarray:
+    """W(Q - G) = W_sinc(Q - G) L(Q - G) (Eqs. weight_sinc, windowed_sinc, lanczos), with
+    dQ = Q - G in supercell-index units [..., 3]; strict window |dQ_alpha| < m_eff."""
+    rcut, meff = lanczos_parameters(m, mprime)
+    dQ = np.asarray(dQ, dtype=np.float64)
+    wsinc = 8.0 * rcut ** 3 * np.prod(sinc(2.0 * math.pi * rcut * dQ), axis=-1)
+    inside = np.all(np.abs(dQ) < meff, axis=-1)
+    L = np.where(inside, np.prod(sinc(math.pi * dQ / meff), axis=-1), 0.0)
+    return wsinc * L
+
+
+def lanczos_support(Q: np.ndarray, m: int, mprime: int = 2) -> np.ndarray:
+    """Integer offsets spanning [floor(Q) - m_eff + 1, floor(Q) + m_eff] per axis (the (2m)^3
+    Bragg positions of Eq. lanczos), rounded outwards for a non-integer m_eff."""
+    _, meff = lanczos_parameters(m, mprime)
+    r = int(math.ceil(meff))
+    off = np.arange(-r + 1, r + 1)
+    return np.stack(np.meshgrid(off, off, off, indexing="ij"), -1).reshape(-1, 3)
+
+
+def lanczos_resample(intensity_at_G, Q: np.ndarray, m: int, mprime: int = 2) -> np.ndarray:
+    """I(Q) ~ sum_G I(G) W(Q - G) / sum_G W(Q - G) (Eq. intensity_convol_finite) for points Q
+    in supercell-index units [nq, 3] (Q_alpha = n_alpha h_alpha, Eq. Q_def).
+
+    `intensity_at_G(G)` returns I at integer supercell Bragg positions G [n, 3]."""
+    Q = np.asarray(Q, dtype=np.float64)
+    off = lanczos_support(Q, m, mprime)
+    base = np.floor(Q).astype(np.int64)
+    G = base[:, None, :] + off[None, :, :]                            # [nq, ntap, 3]
+    W = lanczos_weight(Q[:, None, :] - G, m, mprime)                  # [nq, ntap]
+    uniq, inv = np.unique(G.reshape(-1, 3), axis=0, return_inverse=True)
+    IG = np.asarray(intensity_at_G(uniq), dtype=np.float64)[inv.reshape(-1)].reshape(W.shape)
+    return np.sum(W * IG, axis=1) / np.sum(W, axis=1)

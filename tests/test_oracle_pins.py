@@ -1,0 +1,478 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix (no GPU needed).
+
+Each test names the passage it pins.  None of them re-types the oracle's own formula: each
+compares against a different route to the same number (a double sum instead of a single sum,
+a brute-force DFT instead of the FFT, a closed form, a symmetry, a finite difference).
+"""
+import itertools
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import core, noise, adjoint
+import synthetic as syn
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _cart_positions(model, m=0, with_u=True):
+    frac, site = core.atom_list(model)
+    A = core.lattice_vectors(model.lattice)
+    r = frac @ A
+    if with_u and model.disp is not None:
+        r = r + model.disp[m].reshape(-1, 3)
+    return r, site
+
+
+# ----------------------------------------------------------------------------------------------
+# geometry
+# ----------------------------------------------------------------------------------------------
+
+def test_reciprocal_lattice_duality_and_hexagonal_d_spacing():
+    """a_i . a*_j = 2 pi delta_ij (Section II definition of a*); hexagonal |Q| = 2 pi / d with
+    the textbook 1/d^2 = 4 (h^2 + h k + k^2) / (3 a^2) + l^2 / c^2."""
+    lat = (4.1, 4.6, 5.2, 84.0, 97.0, 101.0)
+    A = core.lattice_vectors(lat)
+    B = core.reciprocal_vectors(lat)
+    assert np.allclose(A @ B.T, 2 * np.pi * np.eye(3), atol=1e-12)
+    assert np.allclose(np.linalg.norm(A, axis=1), lat[:3])
+    # Cartesian frame of the boundary: a along x, b in the xy plane, c with positive z
+    assert abs(A[0, 1]) + abs(A[0, 2]) + abs(A[1, 2]) == 0.0 and A[0, 0] > 0 and A[2, 2] > 0
+    cosg = np.dot(A[0], A[1]) / (lat[0] * lat[1])
+    assert math.isclose(math.degrees(math.acos(cosg)), lat[5], rel_tol=1e-12)
+    a, c = 3.3, 5.1
+    hex_lat = (a, a, c, 90.0, 90.0, 120.0)
+    for h, k, l in [(1, 0, 0), (1, 1, 0), (2, -1, 3), (0, 0, 2), (3, 2, 1)]:
+        inv_d2 = 4.0 * (h * h + h * k + k * k) / (3 * a * a) + l * l / (c * c)
+        q = np.linalg.norm(core.q_cart(np.array([[h, k, l]]), hex_lat))
+        assert math.isclose(q, 2 * np.pi * math.sqrt(inv_d2), rel_tol=1e-12)
+
+
+def test_form_factor_special_values():
+    """s = 0 gives sum of amplitudes; large s leaves the constant term; <j0> of the magnetic
+    workload at s^2 = 0.1 by hand."""
+    g4 = np.array([1.0, 2.0, 3.0, 4.0, 10.0, 20.0, 30.0, 40.0, 0.5])
+    assert math.isclose(core.form_factor(1, g4, np.array([0.0]))[0], 10.5)
+    assert math.isclose(core.form_factor(1, g4, np.array([1e4]))[0], 0.5, abs_tol=1e-12)
+    j0 = np.array(list(syn.J0_COEF) + [0, 0])
+    q = 4 * np.pi * math.sqrt(0.1)
+    want = 0.4 * math.exp(-1.5) + 0.6 * math.exp(-0.5) + 0.0 * math.exp(-0.1) + 0.0
+    assert math.isclose(core.form_factor(2, j0, np.array([q]))[0], want, rel_tol=1e-14)
+
+
+# ----------------------------------------------------------------------------------------------
+# part 1: the direct sum
+# ----------------------------------------------------------------------------------------------
+
+def _double_sum_intensity(r, amp, site, ff_kind, ff_coef, lattice, hkl):
+    """Eq. intensity_dble_sum: I = (1/N) sum_{j,k} a_j a_k exp(i Q.(r_j - r_k)), pure Python."""
+    B = core.reciprocal_vectors(lattice)
+    out = []
+    for h in hkl:
+        Q = h @ B
+        qn = float(np.linalg.norm(Q))
+        f = [core.form_factor(int(ff_kind[s]), ff_coef[s], np.array([qn]))[0] for s in site]
+        acc = 0.0 + 0.0j
+        for j in range(len(amp)):
+            for k in range(len(amp)):
+                acc += amp[j] * f[j] * amp[k] * f[k] * np.exp(1j * float(Q @ (r[j] - r[k])))
+        out.append(acc.real / len(amp))
+    return np.array(out)
+
+
+def test_direct_sum_matches_double_sum():
+    """Eq. intensity_sf with Eq. sf equals Eq. intensity_dble_sum (the factorisation of
+    Section II), on <= 50 atoms with displacements, mixed form factors, triclinic cell."""
+    m = syn.small_case(syn.DISP, cells=(3, 2, 2), nsite=4, nmodels=1, seed=5, sigma=0.2)
+    frac, site = core.atom_list(m)
+    r, _ = _cart_positions(m)
+    w = core.displacive_weights(m, 0)
+    rng = np.random.default_rng(0)
+    hkl = rng.uniform(-2.5, 2.5, (12, 3))
+    I1 = core.displacive_intensity_direct(m, hkl, core.TOTAL)
+    I2 = _double_sum_intensity(r, w, site, m.ff_kind, m.ff_coef, m.lattice, hkl)
+    assert frac.shape[0] <= 50
+    np.testing.assert_allclose(I1, I2, rtol=1e-11, atol=1e-12 * np.max(I2))
+
+
+def test_direct_sum_supercell_translation_invariance():
+    """I(G) is unchanged when an atom moves by a supercell lattice vector, since
+    exp(+-i G.n) = 1 (Section II); at an incommensurate Q it changes."""
+    m = syn.small_case(syn.DISP, cells=(3, 4, 2), nsite=2, nmodels=1, seed=8)
+    frac, site = core.atom_list(m)
+    u = m.disp[0].reshape(-1, 3).astype(np.float64)
+    w = core.displacive_weights(m, 0)
+    G = np.array([[1, 2, -3], [4, -1, 0], [-2, 5, 3], [0, 0, 1]])
+    hkl = G / np.array(m.cells)
+    frac2 = frac.copy()
+    frac2[5] += np.array(m.cells) * np.array([1, -2, 1])
+    F1 = core.structure_factor(frac, u, w, site, m.ff_kind, m.ff_coef, m.lattice, hkl)
+    F2 = core.structure_factor(frac2, u, w, site, m.ff_kind, m.ff_coef, m.lattice, hkl)
+    np.testing.assert_allclose(F1, F2, rtol=1e-12, atol=1e-12)
+    hq = np.array([[0.13, 0.41, -0.37]])
+    Fa = core.structure_factor(frac, u, w, site, m.ff_kind, m.ff_coef, m.lattice, hq)
+    Fb = core.structure_factor(frac2, u, w, site, m.ff_kind, m.ff_coef, m.lattice, hq)
+    assert abs(Fa - Fb).max() > 1e-3
+
+
+def test_undisplaced_fcc_closed_form():
+    """Zero disorder, fcc with f = 1: I(H) = N for unmixed hkl, 0 for mixed hkl, and
+    I(G) = 0 off the unit-cell Bragg positions (k != 0), for the direct sum and both FFT
+    routes (occupancy with delta = 1, displacive with u = 0)."""
+    cells = (4, 3, 2)
+    m = syn.displacive_fcc(cells=cells, sigma=0.0, seed=1)
+    m.disp[:] = 0.0
+    G = np.stack(np.meshgrid(np.arange(-8, 8), np.arange(-6, 6), np.arange(-4, 4),
+                             indexing="ij"), -1).reshape(-1, 3)
+    hkl = G / np.array(cells)
+    integer = np.all(np.mod(G, cells) == 0, axis=1)
+    H = (G // np.array(cells))
+    unmixed = np.all(np.mod(H, 2) == 0, axis=1) | np.all(np.mod(H, 2) == 1, axis=1)
+    want = np.where(integer & unmixed, m.natom, 0.0)
+    I_dir = core.displacive_intensity_direct(m, hkl, core.TOTAL)
+    np.testing.assert_allclose(I_dir, want, atol=1e-9 * m.natom)
+    I_fft = core.displacive_intensity_fft(m, G, core.TOTAL, P=3)
+    np.testing.assert_allclose(I_fft, want, atol=1e-9 * m.natom)
+    m.occ = np.ones((1, 4) + cells, dtype=np.uint8)
+    I_occ = core.occupancy_intensity_fft(m, G, core.TOTAL)
+    np.testing.assert_allclose(I_occ, want, atol=1e-9 * m.natom)
+    # DIFFUSE with delta = 1 and u = 0 has nothing left
+    assert np.max(np.abs(core.occupancy_intensity_fft(m, G, core.DIFFUSE))) < 1e-9
+    assert np.max(np.abs(core.occupancy_intensity_direct(m, hkl, core.DIFFUSE))) < 1e-9 * m.natom
+
+
+@pytest.mark.parametrize("kind", [syn.OCC, syn.SPIN, syn.DISP])
+def test_friedel_symmetry(kind):
+    """I(Q) = I(-Q) for real amplitudes (all three disorder types, both modes)."""
+    m = syn.small_case(kind, cells=(3, 4, 3), nsite=3, nmodels=2, seed=21)
+    rng = np.random.default_rng(3)
+    hkl = rng.uniform(-2, 2, (20, 3))
+    hkl[:4] = np.rint(hkl[:4])                 # include integer (Bragg) points
+    both = np.concatenate([hkl, -hkl])
+    for mode in (core.TOTAL, core.DIFFUSE):
+        if kind == syn.OCC:
+            I = core.occupancy_intensity_direct(m, both, mode)
+        elif kind == syn.SPIN:
+            I = core.magnetic_intensity_direct(m, both, mode)
+        else:
+            I = core.displacive_intensity_direct(m, both, mode)
+        np.testing.assert_allclose(I[:20], I[20:], rtol=1e-10, atol=1e-12 * I.max())
+
+
+def test_magnetic_projection_special_cases():
+    """Eqs. mag_intensity, mag_projection: a single moment parallel to Q^ scatters nothing; a
+    moment perpendicular to Q^ gives C |F|^2 / N; at Q = 0 the orientational average 2/3."""
+    m = syn.small_case(syn.SPIN, cells=(1, 1, 1), nsite=1, nmodels=1, seed=2)
+    m.ff_kind[:] = 0
+    m.scat_len[:] = 1.0
+    hkl = np.array([[0.3, -0.2, 0.7]])
+    Q = core.q_cart(hkl, m.lattice)[0]
+    qhat = Q / np.linalg.norm(Q)
+    perp = np.cross(qhat, [0.3, 0.5, 0.1])
+    perp /= np.linalg.norm(perp)
+    m.spins = np.zeros((1, 1, 1, 1, 1, 3), dtype=np.float32)
+    m.spins[..., :] = qhat.astype(np.float32)
+    assert core.magnetic_intensity_direct(m, hkl)[0] < 1e-12
+    m.spins[..., :] = perp.astype(np.float32)
+    s = float(np.linalg.norm(m.spins[0, 0, 0, 0, 0].astype(np.float64)))
+    assert math.isclose(core.magnetic_intensity_direct(m, hkl)[0], core.C_MAG * s * s, rel_tol=1e-9)
+    I0 = core.magnetic_intensity_direct(m, np.zeros((1, 3)))[0]
+    assert math.isclose(I0, core.C_MAG * (2.0 / 3.0) * s * s, rel_tol=1e-9)
+    assert core.C_MAG == 0.07265
+
+
+# ----------------------------------------------------------------------------------------------
+# part 2: the FFT method
+# ----------------------------------------------------------------------------------------------
+
+def test_lattice_fft_matches_brute_force_dft():
+    """Eq. fft (sign +i, no normalisation) against an O(n^6) loop, on a 4 x 3 x 5 grid; delta,
+    constant and plane-wave special cases."""
+    rng = np.random.default_rng(1)
+    n = (4, 3, 5)
+    x = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    X = core.lattice_fft(x)
+    for k in itertools.product(*(range(a) for a in n)):
+        acc = 0.0 + 0.0j
+        for R in itertools.product(*(range(a) for a in n)):
+            acc += x[R] * np.exp(2j * np.pi * sum(k[a] * R[a] / n[a] for a in range(3)))
+        assert abs(X[k] - acc) < 1e-11
+    d = np.zeros(n)
+    d[1, 2, 3] = 1.0
+    kk = np.stack(np.meshgrid(*(np.arange(a) for a in n), indexing="ij"), -1)
+    want = np.exp(2j * np.pi * (kk[..., 0] * 1 / 4 + kk[..., 1] * 2 / 3 + kk[..., 2] * 3 / 5))
+    np.testing.assert_allclose(core.lattice_fft(d), want, atol=1e-12)
+    c = core.lattice_fft(np.ones(n))
+    assert abs(c[0, 0, 0] - 60) < 1e-12 and np.abs(c).sum() - 60 < 1e-10
+    R = np.stack(np.meshgrid(*(np.arange(a) for a in n), indexing="ij"), -1)
+    k0 = (1, 2, 4)
+    pw = np.exp(-2j * np.pi * sum(k0[a] * R[..., a] / n[a] for a in range(3)))
+    P = core.lattice_fft(pw)
+    assert abs(P[k0] - 60) < 1e-10 and np.abs(P).sum() - 60 < 1e-9
+
+
+def test_parseval():
+    """sum_k |X_k|^2 = n1 n2 n3 sum_R |x_R|^2 for every transformed field."""
+    rng = np.random.default_rng(2)
+    x = rng.standard_normal((2, 6, 5, 4))
+    X = core.lattice_fft(x)
+    np.testing.assert_allclose(np.sum(np.abs(X) ** 2, axis=(1, 2, 3)),
+                               120 * np.sum(x ** 2, axis=(1, 2, 3)), rtol=1e-12)
+
+
+def _grid_G(model):
+    return model.qgrid.g_index(model.cells)
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_fft_method_equals_direct_sum_occupancy(mode):
+    """'Calculations using the DFT and the FFT gave identical results' (Section IV) for
+    compositional disorder, Eqs. comp_sf_diffuse..comp_diffuse_intensity: equal to rounding."""
+    m = syn.small_case(syn.OCC, cells=(4, 3, 5), nsite=3, nmodels=2, seed=31)
+    G = _grid_G(m)
+    hkl = G / np.array(m.cells)
+    I_fft = core.occupancy_intensity_fft(m, G, mode)
+    I_dir = core.occupancy_intensity_direct(m, hkl, mode)
+    np.testing.assert_allclose(I_fft, I_dir, rtol=1e-9, atol=1e-11 * I_dir.max())
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_fft_method_equals_direct_sum_magnetic(mode):
+    """Same for magnetic disorder, Eqs. mag_sf..mag_projection, incl. the G = 0 voxel."""
+    m = syn.small_case(syn.SPIN, cells=(3, 4, 3), nsite=3, nmodels=2, seed=32)
+    G = _grid_G(m)
+    assert np.any(np.all(G == 0, axis=1))
+    hkl = G / np.array(m.cells)
+    I_fft = core.magnetic_intensity_fft(m, G, mode)
+    I_dir = core.magnetic_intensity_direct(m, hkl, mode)
+    np.testing.assert_allclose(I_fft, I_dir, rtol=1e-9, atol=1e-11 * I_dir.max())
+
+
+@pytest.mark.parametrize("mode,P", [(0, 4), (1, 4), (1, 8), (0, 14)])
+def test_taylor_fft_within_remainder_bound(mode, P):
+    """Section III C: the order-P Taylor FFT method differs from the exact direct sum by no
+    more than the remainder bound, voxel by voxel; at high order it converges to rounding."""
+    m = syn.small_case(syn.DISP, cells=(3, 4, 2), nsite=3, nmodels=2, seed=33, sigma=0.15)
+    G = _grid_G(m)
+    hkl = G / np.array(m.cells)
+    I_dir, F = core.displacive_intensity_direct(m, hkl, mode, return_F=True)
+    I_fft = core.displacive_intensity_fft(m, G, mode, P=P)
+    bound = core.truncation_bound(m, hkl, P, mode, F=F)
+    assert np.all(np.abs(I_fft - I_dir) <= bound * (1 + 1e-9) + 1e-12 * I_dir.max())
+    if P >= 14:
+        assert np.max(np.abs(I_fft - I_dir)) < 1e-9 * I_dir.max()
+    else:
+        assert np.max(np.abs(I_fft - I_dir)) > 1e-14   # the truncation is visible
+
+
+def test_monomial_enumeration_counts():
+    """(n+1)(n+2)/2 FFTs for order n; the fifth-order pure-displacive example needs 55 FFTs
+    (Section IV: the order-0 field of a pure displacive model is constant)."""
+    with open(os.path.join(GOLDEN, "paper_constants.json")) as f:
+        gold = json.load(f)
+    mons = core.monomials(5)
+    assert len(mons) - 1 == gold["ffts_fifth_order_displacive"]["value"] == 55
+    for P in range(12):
+        mons = core.monomials(P)
+        assert len(set(mons)) == len(mons) == (P + 1) * (P + 2) * (P + 3) // 6
+        for n in range(P + 1):
+            assert sum(1 for t in mons if sum(t) == n) == (n + 1) * (n + 2) // 2
+        assert [sum(t) for t in mons] == sorted(sum(t) for t in mons)
+
+
+def test_taylor_order_and_x_max():
+    """The chosen order is the first whose remainder bound x^(P+1)/(P+1)! is below eps, and
+    x_max (box corners) equals the brute-force maximum of |Q.u| over every grid point."""
+    for x, eps in [(4.6, 1e-8), (9.7, 1e-5), (0.3, 1e-12), (1.0, 0.3)]:
+        P = core.taylor_order(x, eps)
+        assert x ** (P + 1) / math.factorial(P + 1) <= eps
+        if P > 0:
+            assert x ** P / math.factorial(P) > eps
+    m = syn.small_case(syn.DISP, cells=(3, 2, 2), nsite=2, nmodels=2, seed=4, sigma=0.2)
+    Q = core.q_cart(m.qgrid.hkl(), m.lattice)
+    u = m.disp.reshape(-1, 3).astype(np.float64)
+    assert math.isclose(core.x_max(m, m.qgrid), float(np.max(np.abs(Q @ u.T))), rel_tol=1e-12)
+
+
+def test_gaussian_displacements_laue_closed_form():
+    """Independent Gaussian displacements (sigma per Cartesian component), f = 1: at every
+    k != 0 voxel E[I] = 1 - exp(-Q^2 sigma^2); at allowed unit-cell Bragg positions the total
+    intensity is N exp(-Q^2 sigma^2) + 1 - exp(-Q^2 sigma^2).  Checked on the 8^3 fcc
+    workload over the full 64^3 grid (speckle averages out over the volume)."""
+    m = syn.displacive_fcc(cells=(8, 8, 8), sigma=0.1, seed=1)
+    G = _grid_G(m)
+    hkl = G / 8.0
+    I = core.displacive_intensity_direct(m, hkl, core.TOTAL)
+    Q2 = np.sum(core.q_cart(hkl, m.lattice) ** 2, axis=1)
+    laue = 1.0 - np.exp(-Q2 * 0.01)
+    off = ~np.all(np.mod(G, 8) == 0, axis=1)
+    ratio = np.mean(I[off] / laue[off])
+    assert abs(ratio - 1.0) < 5.0 / math.sqrt(off.sum() / 2)
+    H = G // 8
+    onb = (~off) & (np.all(H % 2 == 0, axis=1) | np.all(H % 2 == 1, axis=1))
+    low = onb & (Q2 * 0.01 < 0.5)
+    want = m.natom * np.exp(-Q2[low] * 0.01) + laue[low]
+    np.testing.assert_allclose(I[low], want, rtol=0.15)
+
+
+# ----------------------------------------------------------------------------------------------
+# noise reduction
+# ----------------------------------------------------------------------------------------------
+
+def test_lanczos_weights_and_normalisation():
+    """Eqs. weight_sinc, windowed_sinc, lanczos: for m = 2 at commensurate Q the 1D taps are
+    1 (centre) and (2/pi)^2 (neighbours), the normalised centre 1/(1 + 8/pi^2); the 3D weight
+    is the product of 1D ones; constant I(G) is reproduced exactly; the 1/m' variant with
+    m = 2 is the squared sinc (Fejer) kernel."""
+    with open(os.path.join(GOLDEN, "paper_constants.json")) as f:
+        gold = json.load(f)
+    d = np.array([[0.0, 0, 0], [1, 0, 0], [2, 0, 0], [1, 1, 0], [1, -1, 1]])
+    W = noise.lanczos_weight(d, 2) / noise.lanczos_weight(np.zeros((1, 3)), 2)[0]
+    nb = gold["lanczos_m2_neighbour_weight"]["value"]
+    assert math.isclose(nb, (2 / math.pi) ** 2, rel_tol=1e-5)
+    np.testing.assert_allclose(W, [1, nb, 0, nb ** 2, nb ** 3], rtol=1e-5, atol=1e-15)
+    w1 = np.array([nb, 1.0, nb])
+    assert math.isclose(1.0 / w1.sum(), gold["lanczos_m2_centre_normalised"]["value"], rel_tol=1e-4)
+    Q = np.array([[3.0, -2.0, 5.0], [0.25, 1.75, -3.5], [7.3, 0.1, -0.9]])
+    out = noise.lanczos_resample(lambda G: np.full(G.shape[0], 4.25), Q, 3)
+    np.testing.assert_allclose(out, 4.25, rtol=1e-13)
+    dd = np.arange(-7, 8, dtype=np.float64)
+    w8 = noise.lanczos_weight(np.stack([dd, 0 * dd, 0 * dd], -1), 2, 8)
+    fej = noise.sinc(np.pi * dd / 8) ** 2
+    np.testing.assert_allclose(w8 / w8[7], fej, rtol=1e-12, atol=1e-15)
+
+
+def test_lanczos_resample_separable():
+    """Separable application along each axis in turn (Section V B) equals the 3D sum."""
+    rng = np.random.default_rng(7)
+    table = {}
+
+    def I_at(G):
+        out = np.empty(G.shape[0])
+        for i, g in enumerate(map(tuple, G)):
+            if g not in table:
+                table[g] = rng.random()
+            out[i] = table[g]
+        return out
+
+    Q = np.array([[2.0, -1.0, 0.0], [4.0, 4.0, -3.0]])
+    full = noise.lanczos_resample(I_at, Q, 2)
+    for qi, q in enumerate(Q):
+        taps = np.arange(-1, 2)
+        w = noise.lanczos_weight(np.stack([taps, 0 * taps, 0 * taps], -1).astype(float), 2)
+        w = w / w.sum()
+        acc = 0.0
+        for a, wa in zip(taps, w):
+            for b, wb in zip(taps, w):
+                for c, wc in zip(taps, w):
+                    acc += wa * wb * wc * I_at(np.array([[q[0] + a, q[1] + b, q[2] + c]]).astype(int))[0]
+        assert math.isclose(full[qi], acc, rel_tol=1e-12)
+
+
+@pytest.mark.parametrize("disorder", ["occ", "spin"])
+def test_subbox_single_cell_closed_form(disorder):
+    """n_sb = 1: every box is one unit cell, so I = (1/(ncell nsite)) sum_R |sum_mu phi_mu x_R|^2
+    (cell-incoherent sum; Section V A with the smallest box)."""
+    kind = syn.OCC if disorder == "occ" else syn.SPIN
+    m = syn.small_case(kind, cells=(3, 2, 3), nsite=3, nmodels=2, seed=41)
+    rng = np.random.default_rng(5)
+    hkl = rng.uniform(-1.5, 1.5, (7, 3))
+    I = noise.subbox_intensity(m, disorder, core.DIFFUSE, 1, hkl)
+    x = noise.subbox_fields(m, disorder, core.DIFFUSE)              # [model][site][...][c]
+    Q = core.q_cart(hkl, m.lattice)
+    f = core.site_form_factors(m, np.linalg.norm(Q, axis=1)) / m.scat_len[None, :]
+    t = hkl @ m.sites.T
+    phi = f * np.exp(2j * np.pi * t)                                # [nq, nsite]
+    acc = np.zeros(hkl.shape[0])
+    for mm in range(m.nmodels):
+        xr = x[mm].reshape(m.nsite, -1, x.shape[-1])                # [site][R][c]
+        F = np.einsum("qs,src->qrc", phi, xr)                        # per cell
+        if disorder == "spin":
+            for r in range(F.shape[1]):
+                acc += core.perp_sq(F[:, r, :], Q)
+        else:
+            acc += np.sum(np.abs(F[..., 0]) ** 2, axis=1)
+    want = acc / (m.nmodels * m.ncell * m.nsite)
+    if disorder == "spin":
+        want = core.C_MAG * want
+    np.testing.assert_allclose(I, want, rtol=1e-10)
+
+
+def test_subbox_pair_sum_form():
+    """The triangular-cutoff reading of Section V A: sum over origins of |F_o|^2 equals
+    sum_{mu,nu} phi_mu conj(phi_nu) sum_Delta w(Delta) exp(iQ.(Delta + r_mu - r_nu)) C(Delta),
+    w(Delta) = prod_alpha (n_sb - |Delta_alpha|), C(Delta) = sum_R x_{R+Delta,mu} x_{R,nu}
+    (periodic), at arbitrary (incommensurate) Q."""
+    m = syn.small_case(syn.OCC, cells=(5, 4, 6), nsite=2, nmodels=1, seed=42)
+    nsb = 2
+    rng = np.random.default_rng(9)
+    hkl = rng.uniform(-1.2, 1.2, (5, 3))
+    I = noise.subbox_intensity(m, "occ", core.TOTAL, nsb, hkl)
+    x = noise.subbox_fields(m, "occ", core.TOTAL)[0, ..., 0]        # [site][n1][n2][n3]
+    Q = core.q_cart(hkl, m.lattice)
+    f = core.site_form_factors(m, np.linalg.norm(Q, axis=1)) / m.scat_len[None, :]
+    acc = np.zeros(hkl.shape[0], dtype=complex)
+    rng_d = range(-nsb + 1, nsb)
+    for mu in range(m.nsite):
+        for nu in range(m.nsite):
+            for D in itertools.product(rng_d, rng_d, rng_d):
+                w = np.prod([nsb - abs(d) for d in D])
+                C = np.sum(np.roll(x[mu], shift=[-d for d in D], axis=(0, 1, 2)) * x[nu])
+                ph = np.exp(2j * np.pi * (hkl @ (np.array(D) + m.sites[mu] - m.sites[nu])))
+                acc += f[:, mu] * f[:, nu] * w * C * ph
+    want = acc.real / (m.ncell * m.nsite * nsb ** 3)
+    np.testing.assert_allclose(I, want, rtol=1e-10)
+
+
+# ----------------------------------------------------------------------------------------------
+# gradient
+# ----------------------------------------------------------------------------------------------
+
+def _fd(fun, model, arr_name, index, h=1e-5):
+    arr = getattr(model, arr_name)
+    base = arr.astype(np.float64)
+    plus, minus = base.copy(), base.copy()
+    plus[index] += h
+    minus[index] -= h
+    setattr(model, arr_name, plus)
+    fp = fun()
+    setattr(model, arr_name, minus)
+    fm = fun()
+    setattr(model, arr_name, arr)
+    return (fp - fm) / (2 * h)
+
+
+def test_displacive_gradient_finite_differences():
+    """Analytic chi^2 gradient vs central differences (FP64, h = 1e-5 A)."""
+    m = syn.small_case(syn.DISP, cells=(2, 3, 2), nsite=2, nmodels=2, seed=51, sigma=0.1)
+    t = syn.small_case(syn.DISP, cells=(2, 3, 2), nsite=2, nmodels=2, seed=52, sigma=0.07)
+    hkl = np.random.default_rng(1).uniform(-2, 2, (40, 3))
+    target = core.displacive_intensity_direct(t, hkl, core.TOTAL)
+    chi2, grad = adjoint.displacive_chi2_grad(m, hkl, target)
+    fun = lambda: float(np.sum((core.displacive_intensity_direct(m, hkl, core.TOTAL) - target) ** 2))
+    assert math.isclose(chi2, fun(), rel_tol=1e-12)
+    for idx in [(0, 0, 0, 0, 0, 0), (1, 1, 1, 2, 1, 2), (0, 1, 1, 0, 0, 1), (1, 0, 0, 1, 1, 0)]:
+        fd = _fd(fun, m, "disp", idx)
+        assert math.isclose(grad[idx], fd, rel_tol=2e-5, abs_tol=1e-7 * np.abs(grad).max())
+
+
+def test_magnetic_gradient_finite_differences():
+    m = syn.small_case(syn.SPIN, cells=(2, 2, 3), nsite=2, nmodels=1, seed=53)
+    t = syn.small_case(syn.SPIN, cells=(2, 2, 3), nsite=2, nmodels=1, seed=54)
+    hkl = np.random.default_rng(2).uniform(-2, 2, (30, 3))
+    hkl[0] = 0.0
+    target = core.magnetic_intensity_direct(t, hkl, core.TOTAL)
+    chi2, grad = adjoint.magnetic_chi2_grad(m, hkl, target)
+    fun = lambda: float(np.sum((core.magnetic_intensity_direct(m, hkl, core.TOTAL) - target) ** 2))
+    for idx in [(0, 0, 0, 0, 0, 0), (0, 1, 1, 1, 2, 2), (0, 1, 0, 1, 1, 1)]:
+        fd = _fd(fun, m, "spins", idx)
+        assert math.isclose(grad[idx], fd, rel_tol=2e-5, abs_tol=1e-7 * np.abs(grad).max())
+
+
+def test_oracle_uses_threads():
+    assert core.oracle_threads() >= 1
+    assert oracle.TOTAL == 0 and oracle.DIFFUSE == 1
