@@ -1,0 +1,380 @@
+#!/usr/bin/env python
+"""Throughput of the FFT-based diffuse-scattering calculation on one GB300 (or N replicas).
+
+Workload (the compositional + magnetic configuration): cubic cell a = 10 A with the 16
+pyrochlore sites, 20x20x20 supercell, Bernoulli(0.3) occupancies and unit spins from
+vMF(kappa = 2) about seeded per-site axes, <j0> magnetic form factor (A=0.4 a=15 B=0.6 b=5 C=0
+c=1 D=0), Q grid |h|,|k|,|l| <= 6 in steps of 1/20 (241^3 = 13,997,521 voxels).  One step =
+the whole hot path for both volumes: per-site FFTs + recombination + |F|^2 (nuclear, diffuse
+mode) and per-site/per-component FFTs + recombination + perpendicular projection (magnetic,
+total mode), FP32 arithmetic.  Metric: intensity voxels/s (both volumes counted), checked
+against the FP64 path of the same kernels (<= 1e-5 of peak).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun each rank runs an independent replica on its own GPU (the workload does not
+shard); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "intensity voxels/s at <=1e-5 rel err vs plain FP64 GPU path"
+UNIT = "voxels/s"
+HMAX, NCELL, NSITE = 6.0, 20, 16
+FP32_FMA_LANES_PER_SM, NUM_SMS = 128, 152
+
+
+def workload_config(extra=None):
+    c = {"workload": "pyrochlore occupancy+magnetic, 16 sites, 20x20x20 cells, |hkl|<=6 step 1/20 "
+                     "(241^3 voxels), nuclear diffuse + magnetic total volumes",
+         "cells": [NCELL] * 3, "nsite": NSITE, "voxels_per_volume": 241 ** 3, "volumes_per_step": 2,
+         "l2": "256 MB memset between steps, outside the per-step events"}
+    if extra:
+        c.update(extra)
+    return c
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def init_dist(backend):
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group(backend=backend)
+    return ws, rank, local
+
+
+def max_over_ranks(x, device=None):
+    ws, _, _ = dist_env()
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(device=None):
+    ws, _, _ = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        if device is not None:
+            dist.barrier(device_ids=[device.index])
+        else:
+            dist.barrier()
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 100 ms while running."""
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 8:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": len(self.rows)}
+        if not self.rows:
+            return out
+        try:
+            sm = [float(r[0]) for r in self.rows]
+            out["sm_mhz"] = statistics.median(sm)
+            out["sm_max_mhz"] = max(float(r[1]) for r in self.rows)
+            out["power_w_max"] = max(float(r[2]) for r in self.rows)
+        except ValueError:
+            pass
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in self.rows:
+            for n, v in zip(names, r[4:8]):
+                if v.strip().lower() == "active":
+                    reasons.add(n)
+        out["reasons"] = sorted(reasons)
+        return out
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+# ----------------------------------------------------------------------------------------------
+# the CPU oracle, timed on the host cores (cpu_baseline leg and --impl reference)
+# ----------------------------------------------------------------------------------------------
+
+def oracle_sample_step(m, mm, zones):
+    """The oracle's FFT method (numpy, FP64) for both volumes on the voxels of `zones`."""
+    import numpy as np
+    from oracle import core
+    G = np.concatenate([z for z in zones])
+    core.occupancy_intensity_fft(m, G, core.DIFFUSE)
+    core.magnetic_intensity_fft(mm, G, core.TOTAL)
+    return 2 * G.shape[0]
+
+
+def zone_voxels(count):
+    import numpy as np
+    rng = np.random.default_rng(12345)
+    out = []
+    k = np.stack(np.meshgrid(*(np.arange(NCELL),) * 3, indexing="ij"), -1).reshape(-1, 3)
+    for _ in range(count):
+        H = rng.integers(-6, 6, 3)
+        out.append(H[None, :] * NCELL + k)
+    return out
+
+
+def cpu_baseline(seconds=12.0):
+    import synthetic as syn
+    m = syn.pyrochlore_occ_mag()
+    mm = syn.magnetic_view(m)
+    t0 = time.perf_counter()
+    vox = oracle_sample_step(m, mm, zone_voxels(1))
+    dt = time.perf_counter() - t0
+    nz = max(1, int(seconds / max(dt, 1e-3)))
+    zones = zone_voxels(nz)
+    t0 = time.perf_counter()
+    vox = oracle_sample_step(m, mm, zones)
+    dt = time.perf_counter() - t0
+    return {"value": vox / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "%d whole H zones (%d voxels per volume, both volumes) of the workload by the oracle's "
+                      "FFT method (numpy FP64, single-threaded), %.1f s" % (nz, vox // 2, dt)}
+
+
+def run_reference(args):
+    ws, rank, local = init_dist("gloo")
+    if rank != 0:
+        return 0
+    import synthetic as syn
+    m = syn.pyrochlore_occ_mag()
+    mm = syn.magnetic_view(m)
+    # size one step to ~1.5 s of CPU work
+    t0 = time.perf_counter()
+    oracle_sample_step(m, mm, zone_voxels(1))
+    dt = time.perf_counter() - t0
+    nz = max(1, int(1.5 / max(dt, 1e-3)))
+    zones = zone_voxels(nz)
+    for _ in range(args.warmup):
+        oracle_sample_step(m, mm, zones)
+    t0 = time.perf_counter()
+    vox = 0
+    for _ in range(args.steps):
+        vox += oracle_sample_step(m, mm, zones)
+    el = time.perf_counter() - t0
+    value = vox / el
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": workload_config({"reference": "CPU FP64 oracle (FFT method, numpy), bounded sample of %d "
+                                                    "H zones per step" % nz}),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": "%d whole H zones per step, both volumes" % nz},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+# ----------------------------------------------------------------------------------------------
+# the GPU path
+# ----------------------------------------------------------------------------------------------
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    ws, rank, local = init_dist("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    import paper_1809_07088_gb300 as ds
+    import synthetic as syn
+
+    m = syn.pyrochlore_occ_mag()
+    mm = syn.magnetic_view(m)
+    q = (m.qgrid.h0, m.qgrid.step, m.qgrid.count)
+    nvox = m.qgrid.nvox
+    ctx = ds.Context(local)
+    lm_n = ds.Model(ctx, m.lattice, m.sites, m.cells, 1, m.scat_len, m.ff_kind, m.ff_coef)
+    lm_m = ds.Model(ctx, mm.lattice, mm.sites, mm.cells, 1, mm.scat_len, mm.ff_kind, mm.ff_coef)
+    occ_h = torch.from_numpy(np.ascontiguousarray(m.occ)).pin_memory()
+    spin_h = torch.from_numpy(np.ascontiguousarray(m.spins)).pin_memory()
+    occ_d, spin_d = occ_h.to(dev), spin_h.to(dev)
+    lm_n.upload_occupancy(occ_d)
+    lm_m.upload_spins(spin_d)
+    I_n = torch.empty(m.qgrid.count, dtype=torch.float32, device=dev)
+    I_m = torch.empty(m.qgrid.count, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step(prec=ds.DS_FP32, outs=(I_n, I_m)):
+        lm_n.intensity(q, out=outs[0], disorder=ds.DS_OCC, mode=ds.DS_DIFFUSE, precision=prec)
+        lm_m.intensity(q, out=outs[1], disorder=ds.DS_SPIN, mode=ds.DS_TOTAL, precision=prec)
+
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    clocks = ClockSampler(local)
+    clocks.start()
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+
+    # timed region: K steps, per-step events on the launching stream, L2 flushed in between
+    buf = ctypes_buf = None
+    import ctypes
+    ctypes_buf = ctypes.create_string_buffer(1 << 16)
+    ctx.lib.ds_profile_report(ctx.h, ctypes_buf, len(ctypes_buf))     # reset counters
+    ctx.lib.ds_profile_enable(ctx.h, 1)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    barrier(dev)
+    torch.cuda.synchronize(dev)
+    t_wall = time.perf_counter()
+    for i in range(args.steps):
+        flush.zero_()
+        ev[i][0].record(stream)
+        step()
+        ev[i][1].record(stream)
+    torch.cuda.synchronize(dev)
+    barrier(dev)
+    t_wall = time.perf_counter() - t_wall
+    ctx.lib.ds_profile_enable(ctx.h, 0)
+    ctx.check(ctx.lib.ds_profile_report(ctx.h, ctypes_buf, len(ctypes_buf)))
+    prof = json.loads(ctypes_buf.value.decode())
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = max_over_ranks(sum(step_ms), dev)
+    vox_step = 2 * nvox
+    value = ws * vox_step * args.steps / (total_ms / 1e3)
+
+    # accuracy of the timed FP32 path against the FP64 path of the same kernels
+    I_n64 = torch.empty(m.qgrid.count, dtype=torch.float64, device=dev)
+    I_m64 = torch.empty(m.qgrid.count, dtype=torch.float64, device=dev)
+    step(ds.DS_FP64, (I_n64, I_m64))
+    torch.cuda.synchronize(dev)
+    errs = []
+    for a, b in ((I_n, I_n64), (I_m, I_m64)):
+        errs.append(float((a.double() - b).abs().max() / b.abs().max()))
+    # plain FP64 path throughput (a few steps)
+    n64 = max(2, min(5, args.steps))
+    e64 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n64)]
+    for i in range(n64):
+        flush.zero_()
+        e64[i][0].record(stream)
+        step(ds.DS_FP64, (I_n64, I_m64))
+        e64[i][1].record(stream)
+    torch.cuda.synchronize(dev)
+    ms64 = sum(a.elapsed_time(b) for a, b in e64) / n64
+
+    # end to end through the public API with host buffers (pinned), copies inside the timed region
+    out_n = torch.empty(m.qgrid.count, dtype=torch.float32).pin_memory()
+    out_m = torch.empty(m.qgrid.count, dtype=torch.float32).pin_memory()
+
+    def e2e_step():
+        lm_n.upload_occupancy(occ_h)
+        lm_m.upload_spins(spin_h)
+        lm_n.intensity(q, out=out_n, disorder=ds.DS_OCC, mode=ds.DS_DIFFUSE, precision=ds.DS_FP32)
+        lm_m.intensity(q, out=out_m, disorder=ds.DS_SPIN, mode=ds.DS_TOTAL, precision=ds.DS_FP32)
+
+    for _ in range(min(3, args.warmup)):
+        e2e_step()
+    torch.cuda.synchronize(dev)
+    barrier(dev)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        e2e_step()
+    torch.cuda.synchronize(dev)
+    e2e_s = max_over_ranks(time.perf_counter() - t0, dev)
+    e2e = {"value": ws * vox_step * args.steps / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": int(occ_h.numel() * occ_h.element_size() + spin_h.numel() * spin_h.element_size()),
+           "d2h_bytes_per_step": int(2 * nvox * 4)}
+
+    # roofline of the dominant kernel: the magnetic recombination (FP32 FMA pipe)
+    peaks, peak_src = measured_peaks()
+    sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    alu_peak = NUM_SMS * FP32_FMA_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+    st = prof["stages"]
+    rec = st.get("recombine_spin", {"count": 1, "ms": float("nan")})
+    avg_ms = rec["ms"] / max(1, rec["count"])
+    flops = nvox * NSITE * 3 * 8              # complex multiply-adds of Eq. mag_sf per voxel
+    achieved = flops / (avg_ms / 1e3) / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
+                "frac": achieved / alu_peak, "traffic": None, "kernel": "k_recomb_cm<float,3,16>",
+                "peak_source": "derived: %d SMs x %d FP32 lanes x 2 flop x %.0f MHz (sm_max_mhz, %s peaks file)"
+                               % (NUM_SMS, FP32_FMA_LANES_PER_SM, sm_mhz, peak_src),
+                "flops_per_launch": flops, "avg_launch_ms": avg_ms}
+    stages = {k: {"count": v["count"], "avg_ms": v["ms"] / max(1, v["count"])} for k, v in st.items()}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline()
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": workload_config({"parallelism": "replicas" if ws > 1 else "single GPU"}),
+            "max_rel_err_vs_fp64": max(errs), "fp64_plain": {"ms_per_step": ms64, "value": ws * vox_step / (ms64 / 1e3)},
+            "e2e": e2e, "roofline": roofline, "stages": stages, "gpu_launches": int(prof.get("launches", 0)),
+            "wall_ms_per_step": 1e3 * t_wall / args.steps, "clocks": clk, "cpu_baseline": cpu}
+    if rank == 0:
+        print(json.dumps(line))
+    lm_n.close()
+    lm_m.close()
+    ctx.close()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

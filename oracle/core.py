@@ -405,26 +405,29 @@ def displacive_intensity_fft(model, G, mode=DIFFUSE, P=None, eps=1e-8, return_F=
     return (I, F) if return_F else I
 
 
-def truncation_bound(model, hkl, P: int, mode=DIFFUSE, F=None):
+def truncation_bound(model, hkl, P: int, mode=DIFFUSE, F=None, chunk=4096):
     """Voxel-wise bound on |I_P - I| from the remainder |x|^(P+1)/(P+1)! of each atom's
     exp(i Q.u) (Section III C): dF = sum_j |w_j f_j| |Q.u_j|^(P+1)/(P+1)!; the Bragg term adds
     the supercell-mean of the same bound at integer H; then |I_P - I| <= (2|F| d + d^2)/N
-    averaged over supercells, with F the exact (direct-sum) structure factor minus <F>."""
+    averaged over supercells, with F the exact (direct-sum) structure factor minus <F>.
+    Evaluated in chunks of Q points to bound memory."""
     _, site = atom_list(model)
-    Q = q_cart(hkl, model.lattice)
-    qn = np.linalg.norm(Q, axis=1)
-    f = np.stack([form_factor(int(model.ff_kind[s]), model.ff_coef[s], qn)
-                  for s in range(model.nsite)], axis=1)
-    ff = np.abs(f)[:, site]                                 # [nq, natom]; b is in w
     lf = math.lgamma(P + 2)
-    dFs = []
-    for m in range(model.nmodels):
-        u = model.disp[m].reshape(-1, 3).astype(np.float64)
-        w = np.abs(displacive_weights(model, m))
-        x = np.abs(Q @ u.T)                                 # [nq, natom]
-        rem = np.exp((P + 1) * np.log(np.maximum(x, 1e-300)) - lf)
-        dFs.append(np.sum(ff * w[None, :] * rem, axis=1))
-    dFs = np.array(dFs)
+    nq = hkl.shape[0]
+    dFs = np.zeros((model.nmodels, nq))
+    for s0 in range(0, nq, chunk):
+        h = hkl[s0:s0 + chunk]
+        Q = q_cart(h, model.lattice)
+        qn = np.linalg.norm(Q, axis=1)
+        f = np.stack([form_factor(int(model.ff_kind[s]), model.ff_coef[s], qn)
+                      for s in range(model.nsite)], axis=1)
+        ff = np.abs(f)[:, site]                             # [nq, natom]; b is in w
+        for m in range(model.nmodels):
+            u = model.disp[m].reshape(-1, 3).astype(np.float64)
+            w = np.abs(displacive_weights(model, m))
+            x = np.abs(Q @ u.T)                             # [nq, natom]
+            rem = np.exp((P + 1) * np.log(np.maximum(x, 1e-300)) - lf)
+            dFs[m, s0:s0 + chunk] = np.sum(ff * w[None, :] * rem, axis=1)
     if mode == DIFFUSE:
         dFs = dFs + is_integer_hkl(hkl)[None, :] * dFs.mean(axis=0)[None, :]
     if F is None:

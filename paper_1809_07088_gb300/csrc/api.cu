@@ -1,0 +1,806 @@
+// C-ABI runtime: contexts, resident supercell models, request planning and the launch sequence
+// of the FFT method (Section III) with the noise-reduction step (Section V).
+//
+// Planning happens on the host in FP64 (grid validation, zone ranges, Taylor order, the
+// monomial list); every step of the calculation itself runs in the kernels of fft.cu,
+// recomb.cu, noise.cu, subbox.cu and adjoint.cu.  Request scratch comes from the device's
+// stream-ordered memory pool (cudaMallocAsync / cudaFreeAsync on the request stream), so
+// repeated requests reuse the same memory without synchronising.
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/ds.h"
+#include "api_internal.h"
+#include "internal.h"
+#include "noise.h"
+
+using namespace ds;
+
+// ------------------------------------------------------------------------------------------
+// errors
+// ------------------------------------------------------------------------------------------
+
+ds_status ds_fail(ds_ctx *ctx, ds_status st, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    if (ctx) {
+        std::lock_guard<std::mutex> g(ctx->err_mu);
+        ctx->err = buf;
+    }
+    return st;
+}
+
+#define CK(call)                                                                                  \
+    do {                                                                                          \
+        cudaError_t e_ = (call);                                                                  \
+        if (e_ != cudaSuccess) return ds_fail(ctx, DS_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+
+// ------------------------------------------------------------------------------------------
+// geometry helpers (host, FP64)
+// ------------------------------------------------------------------------------------------
+
+static void lattice_matrices(const double lat[6], double A[9], double B[9]) {
+    const double d2r = 3.14159265358979323846 / 180.0;
+    const double a = lat[0], b = lat[1], c = lat[2];
+    const double al = lat[3] * d2r, be = lat[4] * d2r, ga = lat[5] * d2r;
+    const double cx = c * cos(be);
+    const double cy = c * (cos(al) - cos(be) * cos(ga)) / sin(ga);
+    const double cz = sqrt(std::max(0.0, c * c - cx * cx - cy * cy));
+    const double Am[9] = {a, 0, 0, b * cos(ga), b * sin(ga), 0, cx, cy, cz};
+    memcpy(A, Am, sizeof(Am));
+    // B rows = 2 pi (A^-1)^T rows: b_i* . a_j = 2 pi delta_ij
+    const double det = Am[0] * (Am[4] * Am[8] - Am[5] * Am[7]) - Am[1] * (Am[3] * Am[8] - Am[5] * Am[6]) +
+                       Am[2] * (Am[3] * Am[7] - Am[4] * Am[6]);
+    double inv[9];
+    inv[0] = (Am[4] * Am[8] - Am[5] * Am[7]) / det;
+    inv[1] = (Am[2] * Am[7] - Am[1] * Am[8]) / det;
+    inv[2] = (Am[1] * Am[5] - Am[2] * Am[4]) / det;
+    inv[3] = (Am[5] * Am[6] - Am[3] * Am[8]) / det;
+    inv[4] = (Am[0] * Am[8] - Am[2] * Am[6]) / det;
+    inv[5] = (Am[2] * Am[3] - Am[0] * Am[5]) / det;
+    inv[6] = (Am[3] * Am[7] - Am[4] * Am[6]) / det;
+    inv[7] = (Am[1] * Am[6] - Am[0] * Am[7]) / det;
+    inv[8] = (Am[0] * Am[4] - Am[1] * Am[3]) / det;
+    const double two_pi = 6.283185307179586476925286766559;
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) B[3 * i + j] = two_pi * inv[3 * j + i];
+}
+
+static bool plan_axis(int n, AxisPlan &p) {
+    p.n = n;
+    p.nrad = 0;
+    int m = n;
+    const int order[5] = {4, 2, 3, 5, 7};
+    for (int r : order) {
+        while (m % r == 0) {
+            if (p.nrad == 8) return false;
+            p.rad[p.nrad++] = r;
+            m /= r;
+        }
+    }
+    return m == 1;
+}
+
+bool make_geometry(const int n[3], Geometry &g) {
+    for (int a = 0; a < 3; ++a) {
+        g.n[a] = n[a];
+        if (n[a] < 1 || n[a] > 128 || !plan_axis(n[a], g.ax[a])) return false;
+    }
+    g.n3h = n[2] / 2 + 1;
+    g.ncell = n[0] * n[1] * n[2];
+    g.ncell_h = n[0] * n[1] * g.n3h;
+    return true;
+}
+
+static int64_t floor_div64(int64_t a, int64_t b) {
+    int64_t q = a / b;
+    if ((a % b != 0) && ((a < 0) != (b < 0))) --q;
+    return q;
+}
+
+// validate a commensurate grid; g0/cnt in supercell indices
+ds_status grid_indices(ds_ctx *ctx, const ds_model *M, const ds_qgrid *q, int g0[3], int cnt[3]) {
+    for (int a = 0; a < 3; ++a) {
+        const double n = M->n[a];
+        if (q->count[a] < 1 || q->count[a] > (1 << 20)) return ds_fail(ctx, DS_ERR_ARG, "grid count[%d] out of range", a);
+        const double s = q->step[a] * n;
+        if (!(fabs(s - 1.0) < 1e-9)) {
+            return ds_fail(ctx, DS_ERR_UNSUPPORTED,
+                           "grid axis %d: step %.17g is not 1/n (only commensurate grids of supercell "
+                           "Bragg positions are handled)", a, q->step[a]);
+        }
+        const double x = q->h0[a] * n;
+        const double r = std::nearbyint(x);
+        if (!(fabs(x - r) < 1e-6)) return ds_fail(ctx, DS_ERR_UNSUPPORTED, "grid axis %d: h0 * n is not integral", a);
+        if (fabs(r) > 1e8) return ds_fail(ctx, DS_ERR_ARG, "grid axis %d: h0 too large", a);
+        g0[a] = (int)r;
+        cnt[a] = (int)q->count[a];
+    }
+    return DS_OK;
+}
+
+GridMap grid_map(const Geometry &g, const int g0[3], const int cnt[3]) {
+    GridMap gm;
+    for (int a = 0; a < 3; ++a) {
+        gm.g0[a] = g0[a];
+        gm.cnt[a] = cnt[a];
+        gm.Hmin[a] = (int)floor_div64(g0[a], g.n[a]);
+        const int Hmax = (int)floor_div64((int64_t)g0[a] + cnt[a] - 1, g.n[a]);
+        gm.nH[a] = Hmax - gm.Hmin[a] + 1;
+    }
+    return gm;
+}
+
+// monomials (a, b, c) with a + b + c <= P in lexicographic order, and the coefficient update
+// code of each (see the displacive recombination kernel)
+void monomial_tables(int P, std::vector<int4> &terms, std::vector<int> &ops) {
+    terms.clear();
+    ops.clear();
+    for (int a = 0; a <= P; ++a)
+        for (int b = 0; b <= P - a; ++b)
+            for (int c = 0; c <= P - a - b; ++c) {
+                terms.push_back(make_int4(a, b, c, a + b + c));
+                int op;
+                if (a == 0 && b == 0 && c == 0) op = 3;
+                else if (c > 0) op = 0;
+                else if (b > 0) op = 1;
+                else op = 2;
+                ops.push_back(op);
+            }
+}
+
+int taylor_order_for(double xmax, double eps) {
+    int P = 0;
+    const double le = log(eps);
+    while ((P + 1) * log(std::max(xmax, 1e-300)) - lgamma((double)P + 2.0) > le) {
+        ++P;
+        if (P > 200) return -1;
+    }
+    return P;
+}
+
+// sites sorted into form-factor classes (contiguous ranges)
+template <typename T>
+static bool form_factor_classes(const ds_model *M, std::vector<int> &site_of, FormFactors<T> &ff) {
+    const int ns = M->nsite;
+    site_of.resize(ns);
+    for (int i = 0; i < ns; ++i) site_of[i] = i;
+    auto key_less = [&](int x, int y) {
+        const int kx = M->ffkind[x], ky = M->ffkind[y];
+        if (kx != ky) return kx < ky;
+        if (kx == DS_FF_CONST) return false;
+        for (int j = 0; j < 9; ++j)
+            if (M->ffcoef[9 * x + j] != M->ffcoef[9 * y + j]) return M->ffcoef[9 * x + j] < M->ffcoef[9 * y + j];
+        return false;
+    };
+    std::stable_sort(site_of.begin(), site_of.end(), key_less);
+    ff.ncls = 0;
+    for (int i = 0; i < ns; ++i) {
+        const bool same = i > 0 && !key_less(site_of[i - 1], site_of[i]) && !key_less(site_of[i], site_of[i - 1]);
+        if (!same) {
+            if (ff.ncls == MAX_FF_CLASSES) return false;
+            const int s = site_of[i];
+            ff.cls_kind[ff.ncls] = M->ffkind[s];
+            for (int j = 0; j < 9; ++j) ff.cls_coef[ff.ncls][j] = (T)M->ffcoef[9 * s + j];
+            ff.ncls++;
+        }
+        ff.cls_end[ff.ncls - 1] = i + 1;
+    }
+    for (int c = ff.ncls; c < MAX_FF_CLASSES; ++c) ff.cls_end[c] = -1;
+    return true;
+}
+
+// ------------------------------------------------------------------------------------------
+// stream-ordered scratch
+// ------------------------------------------------------------------------------------------
+
+Scratch::~Scratch() { release(); }
+void *Scratch::get(size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    void *p = nullptr;
+    cudaError_t e = cudaMallocAsync(&p, bytes, stream);
+    if (e != cudaSuccess) {
+        failed = true;
+        cudaGetLastError();
+        return nullptr;
+    }
+    ptrs.push_back(p);
+    total += bytes;
+    return p;
+}
+void Scratch::release() {
+    for (void *p : ptrs) cudaFreeAsync(p, stream);
+    ptrs.clear();
+}
+
+// ------------------------------------------------------------------------------------------
+// context and models
+// ------------------------------------------------------------------------------------------
+
+extern "C" const char *ds_version(void) { return "paper_1809_07088_gb300 0.1 (sm_103a)"; }
+
+extern "C" ds_status ds_create(ds_ctx **out, int device, size_t budget) {
+    if (!out) return DS_ERR_ARG;
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+        cudaGetLastError();
+        return DS_ERR_ARG;
+    }
+    if (cudaSetDevice(device) != cudaSuccess) return DS_ERR_CUDA;
+    ds_ctx *ctx = new ds_ctx();
+    ctx->device = device;
+    size_t fr = 0, tot = 0;
+    cudaMemGetInfo(&fr, &tot);
+    ctx->budget = budget ? budget : (size_t)(0.9 * (double)fr);
+    if (cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess) {
+        delete ctx;
+        return DS_ERR_CUDA;
+    }
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess) {
+        uint64_t thr = UINT64_MAX;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+    cudaGetLastError();
+    *out = ctx;
+    return DS_OK;
+}
+
+extern "C" ds_status ds_destroy(ds_ctx *ctx) {
+    if (!ctx) return DS_ERR_ARG;
+    serving_shutdown(ctx);
+    cudaSetDevice(ctx->device);
+    cudaStreamSynchronize(ctx->stream);
+    for (ds_model *m : std::vector<ds_model *>(ctx->models.begin(), ctx->models.end())) ds_model_destroy(m);
+    cudaStreamDestroy(ctx->stream);
+    delete ctx;
+    return DS_OK;
+}
+
+extern "C" const char *ds_last_error(const ds_ctx *ctx) {
+    if (!ctx) return "null context";
+    return ctx->err.c_str();
+}
+
+extern "C" ds_status ds_model_create(ds_ctx *ctx, ds_model **out) {
+    if (!ctx || !out) return ds_fail(ctx, DS_ERR_ARG, "null argument");
+    ds_model *m = new ds_model();
+    m->ctx = ctx;
+    ctx->models.insert(m);
+    *out = m;
+    return DS_OK;
+}
+
+static void free_arrays(ds_model *m) {
+    cudaSetDevice(m->ctx->device);
+    cudaStreamSynchronize(m->ctx->stream);
+    if (m->d_occ) cudaFree(m->d_occ);
+    if (m->d_spins) cudaFree(m->d_spins);
+    if (m->d_disp) cudaFree(m->d_disp);
+    m->d_occ = nullptr;
+    m->d_spins = nullptr;
+    m->d_disp = nullptr;
+}
+
+extern "C" ds_status ds_model_destroy(ds_model *m) {
+    if (!m) return DS_ERR_ARG;
+    free_arrays(m);
+    if (m->d_sites) cudaFree(m->d_sites);
+    m->ctx->models.erase(m);
+    delete m;
+    return DS_OK;
+}
+
+extern "C" ds_status ds_model_set_lattice(ds_model *m, double a, double b, double c, double al, double be,
+                                          double ga) {
+    if (!m) return DS_ERR_ARG;
+    ds_ctx *ctx = m->ctx;
+    if (!(a > 0 && b > 0 && c > 0) || !(al > 0 && al < 180 && be > 0 && be < 180 && ga > 0 && ga < 180))
+        return ds_fail(ctx, DS_ERR_ARG, "invalid lattice parameters");
+    const double lat[6] = {a, b, c, al, be, ga};
+    double A[9], B[9];
+    lattice_matrices(lat, A, B);
+    if (!(A[8] > 0) || !std::isfinite(B[0])) return ds_fail(ctx, DS_ERR_ARG, "degenerate lattice");
+    memcpy(m->lat, lat, sizeof(lat));
+    memcpy(m->A, A, sizeof(A));
+    memcpy(m->recip, B, sizeof(B));
+    m->has_lattice = true;
+    return DS_OK;
+}
+
+extern "C" ds_status ds_model_set_sites(ds_model *m, int nsite, const double *xyz, const double *scat,
+                                        const int *kind, const double *coef) {
+    if (!m) return DS_ERR_ARG;
+    ds_ctx *ctx = m->ctx;
+    if (nsite < 1 || nsite > MAX_SITES || !xyz) return ds_fail(ctx, DS_ERR_ARG, "nsite must be 1..%d", MAX_SITES);
+    for (int i = 0; i < nsite; ++i) {
+        if (kind && (kind[i] < 0 || kind[i] > 2)) return ds_fail(ctx, DS_ERR_ARG, "form-factor kind of site %d", i);
+        for (int a = 0; a < 3; ++a)
+            if (!std::isfinite(xyz[3 * i + a])) return ds_fail(ctx, DS_ERR_ARG, "site %d coordinate", i);
+    }
+    free_arrays(m);
+    m->has_occ = m->has_spins = m->has_disp = false;
+    m->nsite = nsite;
+    m->sites.assign(xyz, xyz + 3 * nsite);
+    m->scat.assign(nsite, 1.0);
+    if (scat) m->scat.assign(scat, scat + nsite);
+    m->ffkind.assign(nsite, DS_FF_CONST);
+    if (kind) m->ffkind.assign(kind, kind + nsite);
+    m->ffcoef.assign(9 * nsite, 0.0);
+    if (coef) m->ffcoef.assign(coef, coef + 9 * nsite);
+    cudaSetDevice(ctx->device);
+    if (m->d_sites) cudaFree(m->d_sites);
+    m->d_sites = nullptr;
+    CK(cudaMalloc(&m->d_sites, sizeof(double) * 3 * nsite));
+    CK(cudaMemcpy(m->d_sites, xyz, sizeof(double) * 3 * nsite, cudaMemcpyHostToDevice));
+    return DS_OK;
+}
+
+extern "C" ds_status ds_model_set_supercell(ds_model *m, int n1, int n2, int n3, int nmodels) {
+    if (!m) return DS_ERR_ARG;
+    ds_ctx *ctx = m->ctx;
+    const int n[3] = {n1, n2, n3};
+    Geometry g;
+    if (nmodels < 1 || nmodels > 100000) return ds_fail(ctx, DS_ERR_ARG, "nmodels out of range");
+    if (!make_geometry(n, g))
+        return ds_fail(ctx, DS_ERR_UNSUPPORTED, "supercell %dx%dx%d: each n must be 1..128 with prime factors 2,3,5,7",
+                       n1, n2, n3);
+    free_arrays(m);
+    m->has_occ = m->has_spins = m->has_disp = false;
+    m->n[0] = n1;
+    m->n[1] = n2;
+    m->n[2] = n3;
+    m->nmodels = nmodels;
+    m->has_cells = true;
+    return DS_OK;
+}
+
+static ds_status upload(ds_model *m, void **dst, const void *src, size_t bytes, int src_dev, void *stream) {
+    ds_ctx *ctx = m->ctx;
+    if (!src) return ds_fail(ctx, DS_ERR_ARG, "null source array");
+    if (!m->has_cells || m->nsite < 1) return ds_fail(ctx, DS_ERR_STATE, "set sites and supercell first");
+    cudaSetDevice(ctx->device);
+    cudaStream_t st = stream ? (cudaStream_t)stream : ctx->stream;
+    if (!*dst) CK(cudaMalloc(dst, bytes));
+    CK(cudaMemcpyAsync(*dst, src, bytes, src_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+    if (!src_dev) CK(cudaStreamSynchronize(st));
+    return DS_OK;
+}
+
+static size_t natoms(const ds_model *m) { return (size_t)m->nmodels * m->nsite * m->n[0] * m->n[1] * m->n[2]; }
+
+extern "C" ds_status ds_model_upload_occupancy(ds_model *m, const uint8_t *occ, const double *mean, int src_dev,
+                                               void *stream) {
+    if (!m) return DS_ERR_ARG;
+    ds_status st = upload(m, (void **)&m->d_occ, occ, natoms(m), src_dev, stream);
+    if (st != DS_OK) return st;
+    m->has_occ = true;
+    m->user_mean = mean != nullptr;
+    if (mean) m->mean_occ.assign(mean, mean + m->nsite);
+    return DS_OK;
+}
+
+extern "C" ds_status ds_model_upload_spins(ds_model *m, const float *spins, int src_dev, void *stream) {
+    if (!m) return DS_ERR_ARG;
+    ds_status st = upload(m, (void **)&m->d_spins, spins, natoms(m) * 3 * sizeof(float), src_dev, stream);
+    if (st == DS_OK) m->has_spins = true;
+    return st;
+}
+
+extern "C" ds_status ds_model_upload_displacements(ds_model *m, const float *disp, int src_dev, void *stream) {
+    if (!m) return DS_ERR_ARG;
+    ds_status st = upload(m, (void **)&m->d_disp, disp, natoms(m) * 3 * sizeof(float), src_dev, stream);
+    if (st == DS_OK) m->has_disp = true;
+    return st;
+}
+
+// ------------------------------------------------------------------------------------------
+// the forward calculation
+// ------------------------------------------------------------------------------------------
+
+ds_status check_request(ds_model *M, const ds_qgrid *q, const ds_opts *o) {
+    ds_ctx *ctx = M->ctx;
+    if (!q || !o) return ds_fail(ctx, DS_ERR_ARG, "null grid or options");
+    if (!M->has_lattice || !M->has_cells || M->nsite < 1) return ds_fail(ctx, DS_ERR_STATE, "model incomplete");
+    if (o->precision != DS_FP32 && o->precision != DS_FP64) return ds_fail(ctx, DS_ERR_ARG, "precision");
+    if (o->mode != DS_TOTAL && o->mode != DS_DIFFUSE) return ds_fail(ctx, DS_ERR_ARG, "mode");
+    if (o->disorder == DS_OCC && !M->has_occ) return ds_fail(ctx, DS_ERR_STATE, "no occupancies uploaded");
+    if (o->disorder == DS_SPIN && !M->has_spins) return ds_fail(ctx, DS_ERR_STATE, "no spins uploaded");
+    if (o->disorder == DS_DISP && !M->has_disp) return ds_fail(ctx, DS_ERR_STATE, "no displacements uploaded");
+    if (o->disorder < 0 || o->disorder > 2) return ds_fail(ctx, DS_ERR_ARG, "disorder");
+    if (o->smoothing == DS_SMOOTH_LANCZOS) {
+        if (o->lanczos_m < 2 || o->lanczos_mprime < 2 || o->lanczos_m * o->lanczos_mprime > 64)
+            return ds_fail(ctx, DS_ERR_ARG, "lanczos m, m' must be >= 2 with m m' <= 64");
+    } else if (o->smoothing == DS_SMOOTH_SUBBOX) {
+        if (o->disorder == DS_DISP)
+            return ds_fail(ctx, DS_ERR_UNSUPPORTED, "sub-box averaging is implemented for occupancy and spin disorder");
+        for (int a = 0; a < 3; ++a)
+            if (o->subbox_n < 1 || 2 * o->subbox_n > M->n[a])
+                return ds_fail(ctx, DS_ERR_ARG, "subbox_n must satisfy 1 <= n_sb <= n_alpha/2");
+    } else if (o->smoothing != DS_SMOOTH_NONE) {
+        return ds_fail(ctx, DS_ERR_ARG, "smoothing");
+    }
+    if (o->disorder == DS_DISP && o->taylor_order < 0 && !(o->taylor_eps > 0 && o->taylor_eps < 1))
+        return ds_fail(ctx, DS_ERR_ARG, "taylor_eps must be in (0, 1) when taylor_order < 0");
+    if (o->disorder == DS_DISP && o->taylor_order > 60) return ds_fail(ctx, DS_ERR_UNSUPPORTED, "taylor_order > 60");
+    if (o->disorder != DS_DISP && M->nsite > 32 && o->disorder == DS_OCC)
+        return ds_fail(ctx, DS_ERR_UNSUPPORTED, "occupancy recombination handles up to 32 sites");
+    if (o->disorder == DS_SPIN && M->nsite > 16)
+        return ds_fail(ctx, DS_ERR_UNSUPPORTED, "magnetic recombination handles up to 16 sites");
+    if (o->disorder == DS_DISP && M->nsite > 16)
+        return ds_fail(ctx, DS_ERR_UNSUPPORTED, "displacive recombination handles up to 16 sites");
+    return DS_OK;
+}
+
+// corners of the box of supercell indices [g0, g0 + cnt - 1], as Cartesian Q
+void box_corners(const ds_model *M, const int g0[3], const int cnt[3], double corners[24]) {
+    int c = 0;
+    for (int i = 0; i < 2; ++i)
+        for (int j = 0; j < 2; ++j)
+            for (int l = 0; l < 2; ++l, ++c) {
+                const double h = (double)(g0[0] + i * (cnt[0] - 1)) / M->n[0];
+                const double k = (double)(g0[1] + j * (cnt[1] - 1)) / M->n[1];
+                const double L = (double)(g0[2] + l * (cnt[2] - 1)) / M->n[2];
+                for (int a = 0; a < 3; ++a)
+                    corners[3 * c + a] = h * M->recip[a] + k * M->recip[3 + a] + L * M->recip[6 + a];
+            }
+}
+
+template <typename T>
+ds_status plan_and_run(ds_model *M, const ds_qgrid *q, const ds_opts *o, T *d_out, cudaStream_t st, Scratch &ws,
+                       ds_result_info *info, ForwardKeep<T> *keep) {
+    using C = c_t<T>;
+    ds_ctx *ctx = M->ctx;
+    int g0[3], cnt[3];
+    ds_status rc = grid_indices(ctx, M, q, g0, cnt);
+    if (rc != DS_OK) return rc;
+    Geometry g;
+    make_geometry(M->n, g);
+    const int nsite = M->nsite, nmod = M->nmodels;
+    const size_t natom = (size_t)nmod * nsite * g.ncell;
+
+    // computing grid: extended by the Lanczos halo on every side
+    int halo = 0;
+    if (o->smoothing == DS_SMOOTH_LANCZOS) halo = lanczos_halo(o->lanczos_m, o->lanczos_mprime);
+    int eg0[3], ecnt[3];
+    for (int a = 0; a < 3; ++a) {
+        eg0[a] = g0[a] - halo;
+        ecnt[a] = cnt[a] + 2 * halo;
+    }
+    const GridMap gm = grid_map(g, eg0, ecnt);
+
+    RecombParams<T> p;
+    memset(&p, 0, sizeof(p));
+    p.g = g;
+    p.gm = gm;
+    p.nsite = nsite;
+    p.nmodels = nmod;
+    p.diffuse = o->mode == DS_DIFFUSE;
+    std::vector<int> site_of;
+    if (!form_factor_classes<T>(M, site_of, p.ff))
+        return ds_fail(ctx, DS_ERR_UNSUPPORTED, "more than %d distinct form factors", MAX_FF_CLASSES);
+    memcpy(p.recip, M->recip, sizeof(p.recip));
+    const double N = (double)nsite * g.ncell;
+    p.norm = (T)(1.0 / (nmod * N));
+    if (o->disorder == DS_SPIN) p.norm = (T)(0.07265 / (nmod * N));  // C of Eq. mag_intensity (barn)
+
+    // small tables
+    p.nmax = std::max(g.n[0], std::max(g.n[1], g.n[2]));
+    p.nHmax = std::max(gm.nH[0], std::max(gm.nH[1], gm.nH[2]));
+    C *phk = (C *)ws.get(sizeof(C) * nsite * 3 * p.nmax);
+    C *phH = (C *)ws.get(sizeof(C) * nsite * 3 * p.nHmax);
+    int *d_site_of = (int *)ws.get(sizeof(int) * nsite);
+    T *d_scat = (T *)ws.get(sizeof(T) * nsite);
+    C *W[3];
+    for (int a = 0; a < 3; ++a) W[a] = (C *)ws.get(sizeof(C) * g.n[a]);
+    double *d_mean = (double *)ws.get(sizeof(double) * nsite * 3);
+    if (ws.failed) return ds_fail(ctx, DS_ERR_OOM, "device allocation failed (tables)");
+    std::vector<T> scat(nsite);
+    for (int i = 0; i < nsite; ++i) scat[i] = (T)M->scat[i];
+    CK(cudaMemcpyAsync(d_site_of, site_of.data(), sizeof(int) * nsite, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(d_scat, scat.data(), sizeof(T) * nsite, cudaMemcpyHostToDevice, st));
+    for (int a = 0; a < 3; ++a) make_twiddles<T>(g.n[a], W[a], st);
+    make_site_tables<T>(g, gm, nsite, M->d_sites, phk, phH, p.nmax, p.nHmax, st);
+    p.phk = phk;
+    p.phH = phH;
+    p.site_of = d_site_of;
+    p.scat = d_scat;
+    p.out = d_out;
+
+    FieldSource src;
+    memset(&src, 0, sizeof(src));
+    src.nsite = nsite;
+    src.diffuse = o->mode == DS_DIFFUSE;
+    int nf_model = 0;
+    int P = 0, Tn = 1;
+    std::vector<int4> terms;
+    std::vector<int> ops;
+    double xmax = -1.0;
+    if (o->disorder == DS_OCC) {
+        src.kind = SRC_OCC;
+        src.occ = M->d_occ;
+        nf_model = nsite;
+        if (src.diffuse) {
+            if (M->user_mean)
+                CK(cudaMemcpyAsync(d_mean, M->mean_occ.data(), sizeof(double) * nsite, cudaMemcpyHostToDevice, st));
+            else
+                site_means_occ(nmod, nsite, g.ncell, M->d_occ, d_mean, st);
+        }
+        src.mean = d_mean;
+        p.ncomp = 1;
+    } else if (o->disorder == DS_SPIN) {
+        src.kind = SRC_SPIN;
+        src.vec3 = M->d_spins;
+        nf_model = 3 * nsite;
+        if (src.diffuse) site_means_spin(nmod, nsite, g.ncell, M->d_spins, d_mean, st);
+        src.mean = d_mean;
+        p.ncomp = 3;
+    } else {
+        double corners[24];
+        box_corners(M, eg0, ecnt, corners);
+        double qscale = 0.0;
+        for (int i = 0; i < 24; ++i) qscale = std::max(qscale, fabs(corners[i]));
+        if (!(qscale > 0)) qscale = 1.0;
+        P = o->taylor_order;
+        if (P < 0) {
+            double *d_corners = (double *)ws.get(sizeof(double) * 24);
+            double *d_x = (double *)ws.get(sizeof(double) * 8);
+            if (ws.failed) return ds_fail(ctx, DS_ERR_OOM, "device allocation failed");
+            CK(cudaMemcpyAsync(d_corners, corners, sizeof(corners), cudaMemcpyHostToDevice, st));
+            corner_xmax((int)natom, M->d_disp, d_corners, d_x, st);
+            double hx[8];
+            CK(cudaMemcpyAsync(hx, d_x, sizeof(hx), cudaMemcpyDeviceToHost, st));
+            CK(cudaStreamSynchronize(st));
+            xmax = 0.0;
+            for (int c = 0; c < 8; ++c) xmax = std::max(xmax, hx[c]);
+            P = taylor_order_for(xmax, o->taylor_eps);
+            if (P < 0 || P > 60) return ds_fail(ctx, DS_ERR_UNSUPPORTED, "Taylor order above 60 (x_max = %g)", xmax);
+        }
+        monomial_tables(P, terms, ops);
+        Tn = (int)terms.size();
+        int4 *d_terms = (int4 *)ws.get(sizeof(int4) * Tn);
+        int *d_ops = (int *)ws.get(sizeof(int) * Tn);
+        T *pw = (T *)ws.get(sizeof(T) * natom * 3 * (P + 1));
+        if (ws.failed) return ds_fail(ctx, DS_ERR_OOM, "device allocation failed (power tables)");
+        CK(cudaMemcpyAsync(d_terms, terms.data(), sizeof(int4) * Tn, cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(d_ops, ops.data(), sizeof(int) * Tn, cudaMemcpyHostToDevice, st));
+        make_powers<T>(g, nmod, nsite, P, qscale, M->d_disp, pw, st);
+        src.kind = SRC_DISP;
+        src.pw = pw;
+        src.terms = d_terms;
+        src.T = Tn;
+        src.P = P;
+        src.occ = M->has_occ ? M->d_occ : nullptr;
+        nf_model = nsite * Tn;
+        p.ncomp = 1;
+        p.nT = Tn;
+        p.ops = d_ops;
+        p.qscale = qscale;
+        if (keep) {
+            keep->terms = d_terms;
+            keep->pw = pw;
+        }
+    }
+    src.nf_per_model = nf_model;
+    const int nf = nf_model * nmod;
+
+    // per-site transforms (Section III)
+    C *spec = (C *)ws.get(sizeof(C) * (size_t)nf * g.ncell_h);
+    const size_t work_cap = 512ull << 20;
+    int fb = (int)std::max<size_t>(1, std::min<size_t>(nf, work_cap / (sizeof(C) * (size_t)g.ncell_h)));
+    C *work = (C *)ws.get(sizeof(C) * (size_t)fb * g.ncell_h);
+    if (ws.failed) return ds_fail(ctx, DS_ERR_OOM, "device allocation failed (spectra: %zu bytes)",
+                                  sizeof(C) * (size_t)nf * g.ncell_h);
+    if (ws.total > ctx->budget)
+        return ds_fail(ctx, DS_ERR_ADMISSION, "request needs %zu bytes of scratch, budget %zu", ws.total, ctx->budget);
+    {
+        ProfScope ps(ctx, "fft", st);
+        for (int f0 = 0; f0 < nf; f0 += fb)
+            fft_real_fields<T>(g, src, f0, std::min(fb, nf - f0), work, spec, W[0], W[1], W[2], st);
+    }
+    p.spec = spec;
+
+    // recombination over the requested voxels (+ Bragg term)
+    if (o->disorder == DS_DISP) {
+        if (p.diffuse) {
+            C *avg0 = (C *)ws.get(sizeof(C) * nsite * Tn);
+            C *bragg = (C *)ws.get(sizeof(C) * (size_t)gm.nH[0] * gm.nH[1] * gm.nH[2]);
+            if (ws.failed) return ds_fail(ctx, DS_ERR_OOM, "device allocation failed");
+            ProfScope ps(ctx, "bragg_disp", st);
+            displacive_bragg<T>(p, src.terms, avg0, bragg, st);
+            p.bragg = bragg;
+        }
+        ProfScope ps(ctx, "recombine_disp", st);
+        for (int m = 0; m < nmod; ++m) {
+            p.model = m;
+            p.accumulate = m > 0;
+            recombine_disp<T>(p, st);
+        }
+    } else {
+        ProfScope ps(ctx, p.ncomp == 1 ? "recombine_occ" : "recombine_spin", st);
+        for (int m = 0; m < nmod; ++m) {
+            p.model = m;
+            p.accumulate = m > 0;
+            recombine_cm<T>(p, st);
+        }
+    }
+    CK(cudaGetLastError());
+    if (keep) {
+        keep->p = p;
+        keep->g = g;
+        keep->src = src;
+        keep->W[0] = W[0];
+        keep->W[1] = W[1];
+        keep->W[2] = W[2];
+    }
+    if (info) {
+        info->taylor_order = P;
+        info->n_monomials = o->disorder == DS_DISP ? Tn : 0;
+        info->x_max = xmax;
+        info->trunc_bound = (o->disorder == DS_DISP && xmax >= 0)
+                                ? exp((P + 1) * log(std::max(xmax, 1e-300)) - lgamma((double)P + 2.0))
+                                : 0.0;
+    }
+    return DS_OK;
+}
+
+template <typename T>
+static ds_status run_intensity(ds_model *M, const ds_qgrid *q, const ds_opts *o, void *out, int out_dev,
+                               cudaStream_t st, ds_result_info *info) {
+    ds_ctx *ctx = M->ctx;
+    int g0[3], cnt[3];
+    ds_status rc = grid_indices(ctx, M, q, g0, cnt);
+    if (rc != DS_OK) return rc;
+    const size_t nvox = (size_t)cnt[0] * cnt[1] * cnt[2];
+    Scratch ws(st);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (!out_dev) {
+        CK(cudaEventCreate(&e0));
+        CK(cudaEventCreate(&e1));
+        CK(cudaEventRecord(e0, st));
+    }
+    T *d_out = out_dev ? (T *)out : (T *)ws.get(sizeof(T) * nvox);
+    if (!d_out) return ds_fail(ctx, DS_ERR_OOM, "device allocation failed (output)");
+    if (o->smoothing == DS_SMOOTH_SUBBOX) {
+        rc = subbox_run<T>(M, q, o, d_out, st, ws, info);
+    } else if (o->smoothing == DS_SMOOTH_LANCZOS) {
+        const int h = lanczos_halo(o->lanczos_m, o->lanczos_mprime);
+        const size_t next = (size_t)(cnt[0] + 2 * h) * (cnt[1] + 2 * h) * (cnt[2] + 2 * h);
+        T *ext = (T *)ws.get(sizeof(T) * next);
+        T *t1 = (T *)ws.get(sizeof(T) * next);
+        T *t2 = (T *)ws.get(sizeof(T) * next);
+        if (ws.failed) return ds_fail(ctx, DS_ERR_OOM, "device allocation failed (Lanczos buffers)");
+        rc = plan_and_run<T>(M, q, o, ext, st, ws, info, nullptr);
+        if (rc == DS_OK) {
+            ProfScope ps(ctx, "lanczos", st);
+            lanczos_resample<T>(ext, t1, t2, d_out, cnt, o->lanczos_m, o->lanczos_mprime, st);
+        }
+    } else {
+        rc = plan_and_run<T>(M, q, o, d_out, st, ws, info, nullptr);
+    }
+    if (rc != DS_OK) {
+        ws.release();
+        cudaStreamSynchronize(st);
+        return rc;
+    }
+    if (info) {
+        info->nvox = (int64_t)nvox;
+        info->workspace_bytes = (int64_t)ws.total;
+        info->gpu_ms = 0.0;
+    }
+    if (!out_dev) {
+        CK(cudaEventRecord(e1, st));
+        CK(cudaMemcpyAsync(out, d_out, sizeof(T) * nvox, cudaMemcpyDeviceToHost, st));
+        ws.release();
+        CK(cudaStreamSynchronize(st));
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (info) info->gpu_ms = ms;
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+    } else {
+        ws.release();
+    }
+    CK(cudaGetLastError());
+    return DS_OK;
+}
+
+extern "C" ds_status ds_request_intensity(ds_model *M, const ds_qgrid *q, const ds_opts *o, void *out,
+                                          int out_is_device, void *stream, ds_result_info *info) {
+    if (!M) return DS_ERR_ARG;
+    ds_ctx *ctx = M->ctx;
+    if (!out) return ds_fail(ctx, DS_ERR_ARG, "null output");
+    ds_status rc = check_request(M, q, o);
+    if (rc != DS_OK) return rc;
+    CK(cudaSetDevice(ctx->device));
+    cudaStream_t st = stream ? (cudaStream_t)stream : ctx->stream;
+    if (o->precision == DS_FP64) return run_intensity<double>(M, q, o, out, out_is_device, st, info);
+    return run_intensity<float>(M, q, o, out, out_is_device, st, info);
+}
+
+template ds_status plan_and_run<float>(ds_model *, const ds_qgrid *, const ds_opts *, float *, cudaStream_t,
+                                       Scratch &, ds_result_info *, ForwardKeep<float> *);
+template ds_status plan_and_run<double>(ds_model *, const ds_qgrid *, const ds_opts *, double *, cudaStream_t,
+                                        Scratch &, ds_result_info *, ForwardKeep<double> *);
+
+// ------------------------------------------------------------------------------------------
+// tracing
+// ------------------------------------------------------------------------------------------
+
+static std::atomic<long long> g_launches{0};
+void ds::count_launches(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+ProfScope::ProfScope(ds_ctx *c, const char *name, cudaStream_t st) : ctx(c), s(st), on(c && c->prof_on) {
+    if (!on) return;
+    rec.name = name;
+    cudaEventCreate(&rec.e0);
+    cudaEventCreate(&rec.e1);
+    cudaEventRecord(rec.e0, s);
+}
+ProfScope::~ProfScope() {
+    if (!on) return;
+    cudaEventRecord(rec.e1, s);
+    std::lock_guard<std::mutex> g(ctx->prof_mu);
+    ctx->prof.push_back(rec);
+}
+
+extern "C" ds_status ds_profile_enable(ds_ctx *ctx, int enable) {
+    if (!ctx) return DS_ERR_ARG;
+    ctx->prof_on = enable != 0;
+    return DS_OK;
+}
+
+extern "C" ds_status ds_profile_report(ds_ctx *ctx, char *json, size_t cap) {
+    if (!ctx || !json) return DS_ERR_ARG;
+    std::vector<ProfRecord> recs;
+    {
+        std::lock_guard<std::mutex> g(ctx->prof_mu);
+        recs.swap(ctx->prof);
+    }
+    std::vector<std::string> names;
+    std::vector<double> ms;
+    std::vector<long> cnt;
+    cudaSetDevice(ctx->device);
+    ds_status rc = DS_OK;
+    for (auto &r : recs) {
+        float t = 0.f;
+        if (cudaEventSynchronize(r.e1) != cudaSuccess || cudaEventElapsedTime(&t, r.e0, r.e1) != cudaSuccess)
+            rc = DS_ERR_CUDA;
+        size_t i = 0;
+        while (i < names.size() && names[i] != r.name) ++i;
+        if (i == names.size()) {
+            names.push_back(r.name);
+            ms.push_back(0.0);
+            cnt.push_back(0);
+        }
+        ms[i] += t;
+        cnt[i] += 1;
+        cudaEventDestroy(r.e0);
+        cudaEventDestroy(r.e1);
+    }
+    std::string out = "{\"stages\": {";
+    for (size_t i = 0; i < names.size(); ++i) {
+        char buf[256];
+        snprintf(buf, sizeof(buf), "%s\"%s\": {\"count\": %ld, \"ms\": %.6f}", i ? ", " : "", names[i].c_str(), cnt[i],
+                 ms[i]);
+        out += buf;
+    }
+    char tail[64];
+    snprintf(tail, sizeof(tail), "}, \"launches\": %lld}", g_launches.exchange(0));
+    out += tail;
+    if (out.size() + 1 > cap) return ds_fail(ctx, DS_ERR_ARG, "profile buffer too small (%zu bytes needed)", out.size() + 1);
+    memcpy(json, out.c_str(), out.size() + 1);
+    if (rc != DS_OK) return ds_fail(ctx, rc, "event timing failed");
+    return DS_OK;
+}

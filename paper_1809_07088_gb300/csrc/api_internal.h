@@ -1,0 +1,119 @@
+// Host-side state behind the opaque C handles, shared by api.cu, serving.cu, subbox.cu and
+// adjoint.cu.
+#pragma once
+
+#include <condition_variable>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <set>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "../../include/ds.h"
+#include "internal.h"
+
+struct ServeJob;
+
+struct ds_model {
+    ds_ctx *ctx = nullptr;
+    double lat[6] = {0};
+    double A[9] = {0}, recip[9] = {0};
+    bool has_lattice = false;
+    int nsite = 0;
+    std::vector<double> sites, scat, ffcoef;
+    std::vector<int> ffkind;
+    int n[3] = {0, 0, 0};
+    int nmodels = 0;
+    bool has_cells = false;
+    uint8_t *d_occ = nullptr;
+    float *d_spins = nullptr;
+    float *d_disp = nullptr;
+    double *d_sites = nullptr;
+    bool has_occ = false, has_spins = false, has_disp = false;
+    bool user_mean = false;
+    std::vector<double> mean_occ;
+};
+
+struct ProfRecord {
+    std::string name;
+    cudaEvent_t e0, e1;
+};
+
+struct ds_ctx {
+    int device = 0;
+    // tracing
+    bool prof_on = false;
+    std::mutex prof_mu;
+    std::vector<ProfRecord> prof;
+    size_t budget = 0;
+    std::mutex err_mu;
+    std::string err;
+    cudaStream_t stream = nullptr;
+    std::set<ds_model *> models;
+    // serving (serving.cu)
+    std::mutex mu;
+    std::condition_variable cv;
+    std::thread worker;
+    bool worker_started = false;
+    bool stop = false;
+    uint64_t next_ticket = 1;
+    std::deque<ServeJob *> queue;
+    std::map<uint64_t, ServeJob *> jobs;
+    size_t inflight_bytes = 0;
+    std::vector<cudaStream_t> serve_streams;
+};
+
+ds_status ds_fail(ds_ctx *ctx, ds_status st, const char *fmt, ...);
+
+// brackets one kernel stage with events when profiling is on
+struct ProfScope {
+    ProfScope(ds_ctx *ctx, const char *name, cudaStream_t s);
+    ~ProfScope();
+    ds_ctx *ctx;
+    cudaStream_t s;
+    ProfRecord rec;
+    bool on;
+};
+
+// stream-ordered scratch of one request
+struct Scratch {
+    explicit Scratch(cudaStream_t s) : stream(s) {}
+    ~Scratch();
+    void *get(size_t bytes);
+    void release();
+    cudaStream_t stream;
+    std::vector<void *> ptrs;
+    size_t total = 0;
+    bool failed = false;
+};
+
+// what the adjoint reuses from the forward plan
+template <typename T> struct ForwardKeep {
+    ds::RecombParams<T> p;
+    ds::Geometry g;
+    ds::FieldSource src;
+    const ds::c_t<T> *W[3];
+    const int4 *terms = nullptr;
+    const T *pw = nullptr;
+};
+
+bool make_geometry(const int n[3], ds::Geometry &g);
+ds::GridMap grid_map(const ds::Geometry &g, const int g0[3], const int cnt[3]);
+ds_status grid_indices(ds_ctx *ctx, const ds_model *M, const ds_qgrid *q, int g0[3], int cnt[3]);
+ds_status check_request(ds_model *M, const ds_qgrid *q, const ds_opts *o);
+void monomial_tables(int P, std::vector<int4> &terms, std::vector<int> &ops);
+int taylor_order_for(double xmax, double eps);
+void box_corners(const ds_model *M, const int g0[3], const int cnt[3], double corners[24]);
+
+// the forward calculation into a device buffer on stream st, scratch from ws
+template <typename T>
+ds_status plan_and_run(ds_model *M, const ds_qgrid *q, const ds_opts *o, T *d_out, cudaStream_t st, Scratch &ws,
+                       ds_result_info *info, ForwardKeep<T> *keep);
+// sub-box averaging (subbox.cu)
+template <typename T>
+ds_status subbox_run(ds_model *M, const ds_qgrid *q, const ds_opts *o, T *d_out, cudaStream_t st, Scratch &ws,
+                     ds_result_info *info);
+// serving (serving.cu)
+void serving_shutdown(ds_ctx *ctx);

@@ -1,0 +1,95 @@
+// Shared device-side definitions of the GB300 diffuse-scattering library.
+//
+// Complex arithmetic on float2 / double2, the per-launch parameter blocks, and the error flag
+// through which kernels report bounded-wait or argument failures to the host.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace ds {
+
+template <typename T> struct cplx;
+template <> struct cplx<float> { using type = float2; };
+template <> struct cplx<double> { using type = double2; };
+template <typename T> using c_t = typename cplx<T>::type;
+
+template <typename T> __host__ __device__ __forceinline__ c_t<T> mk(T re, T im) {
+    c_t<T> z;
+    z.x = re;
+    z.y = im;
+    return z;
+}
+template <typename C> __host__ __device__ __forceinline__ C cadd(C a, C b) {
+    a.x += b.x;
+    a.y += b.y;
+    return a;
+}
+template <typename C> __host__ __device__ __forceinline__ C csub(C a, C b) {
+    a.x -= b.x;
+    a.y -= b.y;
+    return a;
+}
+template <typename C> __host__ __device__ __forceinline__ C cmul(C a, C b) {
+    C z;
+    z.x = a.x * b.x - a.y * b.y;
+    z.y = a.x * b.y + a.y * b.x;
+    return z;
+}
+template <typename C> __host__ __device__ __forceinline__ C cconj(C a) {
+    a.y = -a.y;
+    return a;
+}
+// a * conj(b)
+template <typename C> __host__ __device__ __forceinline__ C cmulc(C a, C b) {
+    C z;
+    z.x = a.x * b.x + a.y * b.y;
+    z.y = a.y * b.x - a.x * b.y;
+    return z;
+}
+template <typename C, typename T> __host__ __device__ __forceinline__ C cscale(C a, T s) {
+    a.x *= s;
+    a.y *= s;
+    return a;
+}
+// acc += a * b
+template <typename C> __device__ __forceinline__ void cfma(C &acc, C a, C b) {
+    acc.x = fma(a.x, b.x, acc.x);
+    acc.x = fma(-a.y, b.y, acc.x);
+    acc.y = fma(a.x, b.y, acc.y);
+    acc.y = fma(a.y, b.x, acc.y);
+}
+// multiply by i^n
+template <typename C> __host__ __device__ __forceinline__ C cipow(C a, int n) {
+    C z;
+    switch (n & 3) {
+    case 0: z = a; break;
+    case 1: z.x = -a.y; z.y = a.x; break;
+    case 2: z.x = -a.x; z.y = -a.y; break;
+    default: z.x = a.y; z.y = -a.x; break;
+    }
+    return z;
+}
+
+// error codes written to the device error word (first writer wins)
+enum : int { DEV_OK = 0, DEV_ERR_TIMEOUT = 1, DEV_ERR_BOUNDS = 2 };
+
+__device__ __forceinline__ void raise_error(int *flag, int code) {
+    if (flag) atomicCAS(flag, 0, code);
+}
+
+constexpr int MAX_SITES = 64;     // sites per unit cell handled by the library
+constexpr int MAX_FF_CLASSES = 8; // distinct non-constant form factors per request
+constexpr double TWO_PI_D = 6.283185307179586476925286766559;
+constexpr double FOUR_PI_D = 12.566370614359172953850573533118;
+
+// form factor of one class at s^2 = (|Q|/4pi)^2; kind 0 = 1, 1 = 4-Gaussian, 2 = <j0>
+template <typename T> __device__ __forceinline__ T form_factor(int kind, const T *c, T s2) {
+    if (kind == 1)
+        return c[0] * exp(-c[4] * s2) + c[1] * exp(-c[5] * s2) + c[2] * exp(-c[6] * s2) +
+               c[3] * exp(-c[7] * s2) + c[8];
+    if (kind == 2) return c[0] * exp(-c[1] * s2) + c[2] * exp(-c[3] * s2) + c[4] * exp(-c[5] * s2) + c[6];
+    return T(1);
+}
+
+} // namespace ds

@@ -1,0 +1,204 @@
+// Batched 3D real-to-half-complex FFT of per-site lattice fields (Eqs. fft, comp_ft, mag_ft,
+// U_fft, A_fft of Section III), unnormalised, sign +i.
+//
+// Pass 1 (planes): one CTA loads `ppc` consecutive R1-planes of one field.  The field values
+// are generated on the fly from the model arrays (occupancy deviation, moment component, or
+// Taylor monomial w u~x^a u~y^b u~z^c / (a! b! c!) built from per-atom power tables), rows
+// R2 = 2p and 2p+1 are packed as one complex line, transformed along axis 3, split into the
+// two half spectra (Hermitian separation), and the half-width plane is transformed along
+// axis 2.  The plane goes to the work buffer [field][R1][k2][k3h].
+// Pass 2 (columns): one CTA loads `cb` consecutive (k2, k3h) columns of one field, transforms
+// them along axis 1 and writes the half spectrum [field][k1][k2][k3h], multiplied by i^n for
+// displacive monomials of order n.  All global traffic is contiguous runs.
+#include <algorithm>
+
+#include "internal.h"
+
+namespace ds {
+
+template <typename T> __global__ void k_twiddles(int n, c_t<T> *W) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n) return;
+    double s, c;
+    sincospi(2.0 * (double)e / (double)n, &s, &c);
+    W[e] = mk<T>((T)c, (T)s);
+}
+
+template <typename T> void make_twiddles(int n, c_t<T> *W, cudaStream_t s) {
+    k_twiddles<T><<<(n + 127) / 128, 128, 0, s>>>(n, W);
+    count_launches(1);
+}
+
+// value of real field f at lattice point `cell` (linear [R1][R2][R3])
+template <typename T>
+__device__ __forceinline__ T source_value(const FieldSource &src, int ncell, int f, int cell) {
+    const int m = f / src.nf_per_model;
+    const int lf = f - m * src.nf_per_model;
+    switch (src.kind) {
+    case SRC_OCC: {
+        const int mu = lf;
+        T v = (T)src.occ[((size_t)m * src.nsite + mu) * ncell + cell];
+        if (src.diffuse) v -= (T)src.mean[mu];
+        return v;
+    }
+    case SRC_SPIN: {
+        const int mu = lf / 3, a = lf - 3 * mu;
+        T v = (T)src.vec3[(((size_t)m * src.nsite + mu) * ncell + cell) * 3 + a];
+        if (src.diffuse) v -= (T)src.mean[mu * 3 + a];
+        return v;
+    }
+    case SRC_DISP: {
+        const int mu = lf / src.T, t = lf - mu * src.T;
+        const int4 e = src.terms[t];
+        const T *pw = (const T *)src.pw;
+        const size_t P1 = (size_t)src.P + 1;
+        const size_t base = (((size_t)m * src.nsite + mu) * 3) * P1 * ncell;
+        T v = pw[base + (0 * P1 + e.x) * ncell + cell] * pw[base + (1 * P1 + e.y) * ncell + cell] *
+              pw[base + (2 * P1 + e.z) * ncell + cell];
+        if (src.occ) v *= (T)src.occ[((size_t)m * src.nsite + mu) * ncell + cell];
+        return v;
+    }
+    default:
+        return ((const T *)src.real_buf)[(size_t)f * ncell + cell];
+    }
+}
+
+template <typename T>
+__global__ void k_fft_planes(Geometry g, FieldSource src, int f0, int ppc, c_t<T> *work, const c_t<T> *W2g,
+                             const c_t<T> *W3g) {
+    using C = c_t<T>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int n1 = g.n[0], n2 = g.n[1], n3 = g.n[2], n3h = g.n3h;
+    const int n2p = (n2 + 1) / 2;
+    const int plane_c = n2p * n3 > n2 * n3h ? n2p * n3 : n2 * n3h;
+    C *W2 = (C *)smem_raw;
+    C *W3 = W2 + n2;
+    C *bufA = W3 + n3;
+    C *bufB = bufA + (size_t)ppc * plane_c;
+    for (int i = threadIdx.x; i < n2; i += blockDim.x) W2[i] = W2g[i];
+    for (int i = threadIdx.x; i < n3; i += blockDim.x) W3[i] = W3g[i];
+
+    const int nchunk = (g.n[0] + ppc - 1) / ppc;
+    const int fl = blockIdx.x / nchunk;
+    const int f = f0 + fl;
+    const int r1_0 = (blockIdx.x - fl * nchunk) * ppc;
+    const int np = min(ppc, n1 - r1_0);
+    const int ncell = g.ncell;
+
+    // load: complex line p of plane q holds rows 2p (real) and 2p + 1 (imaginary)
+    const int per_plane_in = n2p * n3;
+    for (int idx = threadIdx.x; idx < np * per_plane_in; idx += blockDim.x) {
+        const int q = idx / per_plane_in, rem = idx - q * per_plane_in;
+        const int p = rem / n3, r3 = rem - p * n3;
+        const int cell0 = ((r1_0 + q) * n2 + 2 * p) * n3 + r3;
+        const T x = source_value<T>(src, ncell, f, cell0);
+        const T y = (2 * p + 1 < n2) ? source_value<T>(src, ncell, f, cell0 + n3) : T(0);
+        bufA[(size_t)q * plane_c + p * n3 + r3] = mk<T>(x, y);
+    }
+    __syncthreads();
+    // axis 3: np * n2p contiguous lines (plane stride plane_c)
+    C *res = fft_lines<T>(bufA, bufB, g.ax[2], W3, np * n2p, n2p, n3, plane_c, 1);
+    C *dst = (res == bufA) ? bufB : bufA;
+    // separate the packed rows: X = (Z + conj Z-)/2, Y = (Z - conj Z-)/(2i), keep k3 < n3h
+    const int per_plane_h = n2 * n3h;
+    for (int idx = threadIdx.x; idx < np * per_plane_h; idx += blockDim.x) {
+        const int q = idx / per_plane_h, rem = idx - q * per_plane_h;
+        const int row = rem / n3h, k3 = rem - row * n3h;
+        const int p = row >> 1;
+        const C z = res[(size_t)q * plane_c + p * n3 + k3];
+        const C zm = res[(size_t)q * plane_c + p * n3 + (n3 - k3) % n3];
+        C v;
+        if ((row & 1) == 0)
+            v = mk<T>(T(0.5) * (z.x + zm.x), T(0.5) * (z.y - zm.y));
+        else
+            v = mk<T>(T(0.5) * (z.y + zm.y), T(-0.5) * (z.x - zm.x));
+        dst[(size_t)q * plane_c + row * n3h + k3] = v;
+    }
+    __syncthreads();
+    // axis 2: np * n3h lines of stride n3h
+    C *res2 = fft_lines<T>(dst, res, g.ax[1], W2, np * n3h, n3h, 1, plane_c, n3h);
+    C *out = work + ((size_t)fl * n1 + r1_0) * per_plane_h;
+    for (int idx = threadIdx.x; idx < np * per_plane_h; idx += blockDim.x) {
+        const int q = idx / per_plane_h, rem = idx - q * per_plane_h;
+        out[(size_t)q * per_plane_h + rem] = res2[(size_t)q * plane_c + rem];
+    }
+}
+
+template <typename T>
+__global__ void k_fft_columns(Geometry g, FieldSource src, int f0, int cb, const c_t<T> *work, c_t<T> *spec,
+                              const c_t<T> *W1g) {
+    using C = c_t<T>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int n1 = g.n[0];
+    const int ncol = g.n[1] * g.n3h;
+    C *W1 = (C *)smem_raw;
+    C *bufA = W1 + n1;
+    C *bufB = bufA + (size_t)n1 * cb;
+    for (int i = threadIdx.x; i < n1; i += blockDim.x) W1[i] = W1g[i];
+    const int nchunk = (ncol + cb - 1) / cb;
+    const int fl = blockIdx.x / nchunk;
+    const int f = f0 + fl;
+    const int c0 = (blockIdx.x - fl * nchunk) * cb;
+    const C *in = work + (size_t)fl * n1 * ncol;
+    for (int idx = threadIdx.x; idx < n1 * cb; idx += blockDim.x) {
+        const int r1 = idx / cb, c = idx - r1 * cb;
+        bufA[idx] = (c0 + c < ncol) ? in[(size_t)r1 * ncol + c0 + c] : mk<T>(T(0), T(0));
+    }
+    __syncthreads();
+    C *res = fft_lines<T>(bufA, bufB, g.ax[0], W1, cb, cb, 1, 0, cb);
+    int rot = 0;
+    if (src.kind == SRC_DISP) {
+        const int lf = f % src.nf_per_model;
+        rot = src.terms[lf % src.T].w;
+    }
+    C *out = spec + (size_t)f * g.ncell_h;
+    for (int idx = threadIdx.x; idx < n1 * cb; idx += blockDim.x) {
+        const int k1 = idx / cb, c = idx - k1 * cb;
+        if (c0 + c < ncol) out[(size_t)k1 * ncol + c0 + c] = cipow(res[idx], rot);
+    }
+}
+
+size_t fft_work_bytes(const Geometry &g, int nf, size_t elem) {
+    return (size_t)nf * g.ncell_h * 2 * elem;
+}
+
+static int plane_batch(const Geometry &g, size_t celem, size_t budget) {
+    const int n2p = (g.n[1] + 1) / 2;
+    const size_t plane_c = (size_t)std::max(n2p * g.n[2], g.n[1] * g.n3h);
+    int ppc = (int)(budget / (2 * plane_c * celem));
+    ppc = std::max(1, std::min(ppc, g.n[0]));
+    return ppc;
+}
+
+template <typename T>
+void fft_real_fields(const Geometry &g, const FieldSource &src, int f0, int nf, c_t<T> *work, c_t<T> *spec,
+                     const c_t<T> *W1, const c_t<T> *W2, const c_t<T> *W3, cudaStream_t s) {
+    using C = c_t<T>;
+    const size_t ce = sizeof(C);
+    // pass 1
+    const int ppc = plane_batch(g, ce, 48 * 1024);
+    const int n2p = (g.n[1] + 1) / 2;
+    const size_t plane_c = (size_t)std::max(n2p * g.n[2], g.n[1] * g.n3h);
+    size_t sm1 = (g.n[1] + g.n[2] + 2 * ppc * plane_c) * ce;
+    if (sm1 > 48 * 1024) cudaFuncSetAttribute(k_fft_planes<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1);
+    dim3 g1((unsigned)(((g.n[0] + ppc - 1) / ppc) * (size_t)nf));
+    k_fft_planes<T><<<g1, 256, sm1, s>>>(g, src, f0, ppc, work, W2, W3);
+    // pass 2
+    const int ncol = g.n[1] * g.n3h;
+    int cb = (int)((48 * 1024 / ce - g.n[0]) / (2 * g.n[0]));
+    cb = std::max(1, std::min(cb, ncol));
+    size_t sm2 = (g.n[0] + 2 * (size_t)g.n[0] * cb) * ce;
+    dim3 g2((unsigned)(((ncol + cb - 1) / cb) * (size_t)nf));
+    k_fft_columns<T><<<g2, 256, sm2, s>>>(g, src, f0, cb, work, spec, W1);
+    count_launches(2);
+}
+
+template void make_twiddles<float>(int, c_t<float> *, cudaStream_t);
+template void make_twiddles<double>(int, c_t<double> *, cudaStream_t);
+template void fft_real_fields<float>(const Geometry &, const FieldSource &, int, int, c_t<float> *, c_t<float> *,
+                                     const c_t<float> *, const c_t<float> *, const c_t<float> *, cudaStream_t);
+template void fft_real_fields<double>(const Geometry &, const FieldSource &, int, int, c_t<double> *,
+                                      c_t<double> *, const c_t<double> *, const c_t<double> *,
+                                      const c_t<double> *, cudaStream_t);
+
+}  // namespace ds

@@ -1,0 +1,598 @@
+// Recombination of the per-site transforms into F(G) and I(G) over every voxel of the
+// requested commensurate grid (Section III, Eqs. total_sf_fin, comp_sf_diffuse,
+// total_sf_taylor, bragg_sf_disp, mag_sf, mag_intensity, mag_projection), plus the small
+// tables it needs (site phases, monomial power tables, site means, x_max for the Taylor order).
+//
+// Every voxel G = H + k (Eq. g_vec) is handled by exactly one thread, so no atomics are used
+// and the result does not depend on scheduling.  Site phases factor as
+// exp(iG.r_mu) = exp(iH.r_mu) exp(ik.r_mu), each a product of three per-axis tables computed
+// in FP64 (exact reduction of the argument modulo 1) and stored in the working precision.
+#include <algorithm>
+
+#include "internal.h"
+
+namespace ds {
+
+// ------------------------------------------------------------------------------------------
+// tables
+// ------------------------------------------------------------------------------------------
+
+template <typename T>
+__global__ void k_site_tables(Geometry g, GridMap gm, int nsite, const double *sites, c_t<T> *phk, c_t<T> *phH,
+                              int nmax, int nHmax) {
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    const int per_site = 3 * (nmax + nHmax);
+    if (idx >= nsite * per_site) return;
+    const int s = idx / per_site;
+    int r = idx - s * per_site;
+    if (r < 3 * nmax) {
+        const int a = r / nmax, kk = r - a * nmax;
+        if (kk >= g.n[a]) return;
+        // k_a r_a / n_a, reduced exactly enough in FP64
+        double t = (double)kk * sites[3 * s + a] / (double)g.n[a];
+        t -= floor(t);
+        double sn, cs;
+        sincospi(2.0 * t, &sn, &cs);
+        phk[((size_t)s * 3 + a) * nmax + kk] = mk<T>((T)cs, (T)sn);
+    } else {
+        r -= 3 * nmax;
+        const int a = r / nHmax, hh = r - a * nHmax;
+        if (hh >= gm.nH[a]) return;
+        double t = (double)(gm.Hmin[a] + hh) * sites[3 * s + a];
+        t -= floor(t);
+        double sn, cs;
+        sincospi(2.0 * t, &sn, &cs);
+        phH[((size_t)s * 3 + a) * nHmax + hh] = mk<T>((T)cs, (T)sn);
+    }
+}
+
+template <typename T>
+void make_site_tables(const Geometry &g, const GridMap &gm, int nsite, const double *sites_dev, c_t<T> *phk,
+                      c_t<T> *phH, int nmax, int nHmax, cudaStream_t s) {
+    const int tot = nsite * 3 * (nmax + nHmax);
+    k_site_tables<T><<<(tot + 255) / 256, 256, 0, s>>>(g, gm, nsite, sites_dev, phk, phH, nmax, nHmax);
+    count_launches(1);
+}
+
+// pw[m][s][a][e][cell] = (u_a Qs)^e / e!, built by the recurrence p_e = p_{e-1} u~ / e in FP64
+template <typename T>
+__global__ void k_powers(int nmodels, int nsite, int ncell, int P, double qscale, const float *disp, T *pw) {
+    const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const size_t natom = (size_t)nmodels * nsite * ncell;
+    if (idx >= natom * 3) return;
+    const int a = (int)(idx / natom);
+    const size_t atom = idx - (size_t)a * natom;        // (m, s, cell) linear
+    const size_t ms = atom / ncell, cell = atom - ms * ncell;
+    const double u = (double)disp[atom * 3 + a] * qscale;
+    T *dst = pw + ((ms * 3 + a) * (size_t)(P + 1)) * ncell + cell;
+    double p = 1.0;
+    dst[0] = (T)1;
+    for (int e = 1; e <= P; ++e) {
+        p = p * u / (double)e;
+        dst[(size_t)e * ncell] = (T)p;
+    }
+}
+
+template <typename T>
+void make_powers(const Geometry &g, int nmodels, int nsite, int P, double qscale, const float *disp, T *pw,
+                 cudaStream_t s) {
+    const size_t n = (size_t)nmodels * nsite * g.ncell * 3;
+    k_powers<T><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(nmodels, nsite, g.ncell, P, qscale, disp, pw);
+    count_launches(1);
+}
+
+__device__ __forceinline__ double block_sum(double v, double *red) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    __syncthreads();
+    if (l == 0) red[w] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (threadIdx.x == 0)
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += red[i];
+    return t;
+}
+
+// one block per (site, component): mean over supercells and lattice points, in FP64
+__global__ void k_means_occ(int nmodels, int nsite, int ncell, const uint8_t *occ, double *mean) {
+    __shared__ double red[32];
+    const int s = blockIdx.x;
+    double acc = 0.0;
+    for (int m = 0; m < nmodels; ++m)
+        for (int c = threadIdx.x; c < ncell; c += blockDim.x) acc += occ[((size_t)m * nsite + s) * ncell + c];
+    const double t = block_sum(acc, red);
+    if (threadIdx.x == 0) mean[s] = t / ((double)nmodels * ncell);
+}
+
+__global__ void k_means_spin(int nmodels, int nsite, int ncell, const float *spins, double *mean) {
+    __shared__ double red[32];
+    const int s = blockIdx.x / 3, a = blockIdx.x % 3;
+    double acc = 0.0;
+    for (int m = 0; m < nmodels; ++m)
+        for (int c = threadIdx.x; c < ncell; c += blockDim.x)
+            acc += spins[(((size_t)m * nsite + s) * ncell + c) * 3 + a];
+    const double t = block_sum(acc, red);
+    if (threadIdx.x == 0) mean[s * 3 + a] = t / ((double)nmodels * ncell);
+}
+
+void site_means_occ(int nmodels, int nsite, int ncell, const uint8_t *occ, double *mean, cudaStream_t s) {
+    k_means_occ<<<nsite, 256, 0, s>>>(nmodels, nsite, ncell, occ, mean);
+    count_launches(1);
+}
+void site_means_spin(int nmodels, int nsite, int ncell, const float *spins, double *mean, cudaStream_t s) {
+    k_means_spin<<<nsite * 3, 256, 0, s>>>(nmodels, nsite, ncell, spins, mean);
+    count_launches(1);
+}
+
+// out[c] = max_j |Q_c . u_j| for the 8 corners of the Q box (non-negative doubles order like
+// their bit patterns, so an integer atomicMax is exact)
+__global__ void k_corner_xmax(int natom, const float *disp, const double *corners, unsigned long long *out) {
+    double best[8];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) best[c] = 0.0;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < natom; j += gridDim.x * blockDim.x) {
+        const double ux = disp[3 * (size_t)j], uy = disp[3 * (size_t)j + 1], uz = disp[3 * (size_t)j + 2];
+#pragma unroll
+        for (int c = 0; c < 8; ++c)
+            best[c] = fmax(best[c], fabs(corners[3 * c] * ux + corners[3 * c + 1] * uy + corners[3 * c + 2] * uz));
+    }
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        double v = best[c];
+        for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
+        if ((threadIdx.x & 31) == 0) atomicMax(out + c, (unsigned long long)__double_as_longlong(v));
+    }
+}
+
+void corner_xmax(int natom, const float *disp, const double *corners, double *out, cudaStream_t s) {
+    cudaMemsetAsync(out, 0, 8 * sizeof(double), s);
+    int nb = std::min(1024, std::max(1, (natom + 255) / 256));
+    k_corner_xmax<<<nb, 256, 0, s>>>(natom, disp, corners, (unsigned long long *)out);
+    count_launches(1);
+}
+
+// ------------------------------------------------------------------------------------------
+// helpers shared by the recombination kernels
+// ------------------------------------------------------------------------------------------
+
+__device__ __forceinline__ int floor_div(int a, int b) {
+    int q = a / b;
+    if ((a % b != 0) && ((a < 0) != (b < 0))) --q;
+    return q;
+}
+__device__ __forceinline__ int ceil_div(int a, int b) { return -floor_div(-a, b); }
+
+// Cartesian Q of G (supercell indices) in FP64
+__device__ __forceinline__ void q_of_G(const double *recip, const int *n, int G1, int G2, int G3, double *Q) {
+    const double h = (double)G1 / n[0], k = (double)G2 / n[1], l = (double)G3 / n[2];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) Q[a] = h * recip[a] + k * recip[3 + a] + l * recip[6 + a];
+}
+
+// ------------------------------------------------------------------------------------------
+// compositional (NC = 1) and magnetic (NC = 3) recombination
+// ------------------------------------------------------------------------------------------
+// CTA: 256 consecutive k (k3 fastest) x a chunk of (H1, H2) zone columns; each thread keeps
+// Y_mu,c(k) = b_mu exp(ik.r_mu) X_mu,c(k) of its k in registers and sweeps the zones, reading
+// exp(iH.r_mu) from a shared-memory table that every thread of the warp reads at once.
+
+template <typename T, int NC, int MAXS>
+__global__ void __launch_bounds__(256) k_recomb_cm(RecombParams<T> p, int h12_per_cta) {
+    using C = c_t<T>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C *Ptab = (C *)smem_raw;
+    const Geometry &g = p.g;
+    const GridMap &gm = p.gm;
+    const int nsite = p.nsite;
+    const int nH12 = gm.nH[0] * gm.nH[1];
+    const int h12_0 = blockIdx.y * h12_per_cta;
+    const int nh12 = min(h12_per_cta, nH12 - h12_0);
+    const int nH3 = gm.nH[2];
+
+    for (int idx = threadIdx.x; idx < nh12 * nH3 * nsite; idx += blockDim.x) {
+        const int s = idx % nsite;
+        const int h3 = (idx / nsite) % nH3;
+        const int j12 = idx / (nsite * nH3);
+        const int h12 = h12_0 + j12;
+        const int h1 = h12 / gm.nH[1], h2 = h12 - h1 * gm.nH[1];
+        const int site = p.site_of[s];
+        const C *t = p.phH + (size_t)site * 3 * p.nHmax;
+        Ptab[idx] = cmul(cmul(t[h1], t[p.nHmax + h2]), t[2 * p.nHmax + h3]);
+    }
+    __syncthreads();
+
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= g.ncell) return;
+    const int k3 = k % g.n[2];
+    const int k2 = (k / g.n[2]) % g.n[1];
+    const int k1 = k / (g.n[2] * g.n[1]);
+
+    // zones along axis 3 reachable from this k3
+    int h3lo = ceil_div(gm.g0[2] - k3, g.n[2]) - gm.Hmin[2];
+    int h3hi = floor_div(gm.g0[2] + gm.cnt[2] - 1 - k3, g.n[2]) - gm.Hmin[2];
+    h3lo = max(h3lo, 0);
+    h3hi = min(h3hi, nH3 - 1);
+
+    int conj;
+    const int kidx = half_index(g, k1, k2, k3, conj);
+    C Y[MAXS][NC];
+#pragma unroll
+    for (int s = 0; s < MAXS; ++s) {
+        if (s < nsite) {
+            const int site = p.site_of[s];
+            const C *t = p.phk + (size_t)site * 3 * p.nmax;
+            const C ph = cscale(cmul(cmul(t[k1], t[p.nmax + k2]), t[2 * p.nmax + k3]), p.scat[site]);
+#pragma unroll
+            for (int c = 0; c < NC; ++c) {
+                C x = p.spec[(((size_t)p.model * nsite + site) * NC + c) * g.ncell_h + kidx];
+                if (conj) x = cconj(x);
+                Y[s][c] = cmul(ph, x);
+            }
+        } else {
+#pragma unroll
+            for (int c = 0; c < NC; ++c) Y[s][c] = mk<T>(T(0), T(0));
+        }
+    }
+
+    for (int j12 = 0; j12 < nh12; ++j12) {
+        const int h12 = h12_0 + j12;
+        const int h1 = h12 / gm.nH[1], h2 = h12 - h1 * gm.nH[1];
+        const int G1 = g.n[0] * (gm.Hmin[0] + h1) + k1;
+        const int G2 = g.n[1] * (gm.Hmin[1] + h2) + k2;
+        if (G1 < gm.g0[0] || G1 >= gm.g0[0] + gm.cnt[0]) continue;
+        if (G2 < gm.g0[1] || G2 >= gm.g0[1] + gm.cnt[1]) continue;
+        const C *Prow = Ptab + (size_t)j12 * nH3 * nsite;
+        const size_t vrow = ((size_t)(G1 - gm.g0[0]) * gm.cnt[1] + (G2 - gm.g0[1])) * gm.cnt[2];
+        for (int h3 = h3lo; h3 <= h3hi; ++h3) {
+            const int G3 = g.n[2] * (gm.Hmin[2] + h3) + k3;
+            double Qd[3];
+            q_of_G(p.recip, g.n, G1, G2, G3, Qd);
+            const T q2 = (T)(Qd[0] * Qd[0] + Qd[1] * Qd[1] + Qd[2] * Qd[2]);
+            const T s2 = q2 * (T)(1.0 / (FOUR_PI_D * FOUR_PI_D));
+            const C *P = Prow + (size_t)h3 * nsite;
+            C F[NC], part[NC];
+#pragma unroll
+            for (int c = 0; c < NC; ++c) F[c] = part[c] = mk<T>(T(0), T(0));
+            int cls = 0;
+#pragma unroll
+            for (int s = 0; s < MAXS; ++s) {
+                if (s < nsite) {
+                    const C ps = P[s];
+#pragma unroll
+                    for (int c = 0; c < NC; ++c) cfma(part[c], ps, Y[s][c]);
+                    if (s + 1 == p.ff.cls_end[cls]) {
+                        const T f = form_factor<T>(p.ff.cls_kind[cls], p.ff.cls_coef[cls], s2);
+#pragma unroll
+                        for (int c = 0; c < NC; ++c) {
+                            F[c].x = fma(f, part[c].x, F[c].x);
+                            F[c].y = fma(f, part[c].y, F[c].y);
+                            part[c] = mk<T>(T(0), T(0));
+                        }
+                        ++cls;
+                    }
+                }
+            }
+            T I;
+            if (NC == 1) {
+                I = F[0].x * F[0].x + F[0].y * F[0].y;
+            } else {
+                T tot = T(0);
+#pragma unroll
+                for (int c = 0; c < NC; ++c) tot += F[c].x * F[c].x + F[c].y * F[c].y;
+                if (q2 > T(0)) {
+                    const T iq = T(1) / sqrt(q2);
+                    const T qx = (T)Qd[0] * iq, qy = (T)Qd[1] * iq, qz = (T)Qd[2] * iq;
+                    const T pr = qx * F[0].x + qy * F[1].x + qz * F[2].x;
+                    const T pi = qx * F[0].y + qy * F[1].y + qz * F[2].y;
+                    I = tot - (pr * pr + pi * pi);
+                } else {
+                    I = T(2) / T(3) * tot;
+                }
+            }
+            const size_t v = vrow + (G3 - gm.g0[2]);
+            const T val = p.norm * I;
+            p.out[v] = p.accumulate ? p.out[v] + val : val;
+        }
+    }
+}
+
+template <typename T, int NC, int MAXS> static void launch_cm(const RecombParams<T> &p, cudaStream_t s) {
+    using C = c_t<T>;
+    const int nH12 = p.gm.nH[0] * p.gm.nH[1];
+    const int ktiles = (p.g.ncell + 255) / 256;
+    // enough CTAs for several waves over 152 SMs
+    int per = std::max(1, (nH12 * ktiles) / (152 * 8));
+    per = std::min(per, nH12);
+    size_t sm = (size_t)per * p.gm.nH[2] * p.nsite * sizeof(C);
+    while (sm > 96 * 1024 && per > 1) {
+        per = (per + 1) / 2;
+        sm = (size_t)per * p.gm.nH[2] * p.nsite * sizeof(C);
+    }
+    if (sm > 48 * 1024)
+        cudaFuncSetAttribute(k_recomb_cm<T, NC, MAXS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    dim3 grid(ktiles, (nH12 + per - 1) / per);
+    k_recomb_cm<T, NC, MAXS><<<grid, 256, sm, s>>>(p, per);
+    count_launches(1);
+}
+
+template <typename T> void recombine_cm(const RecombParams<T> &p, cudaStream_t s) {
+    if (p.ncomp == 1) {
+        if (p.nsite <= 4) launch_cm<T, 1, 4>(p, s);
+        else if (p.nsite <= 8) launch_cm<T, 1, 8>(p, s);
+        else if (p.nsite <= 16) launch_cm<T, 1, 16>(p, s);
+        else launch_cm<T, 1, 32>(p, s);
+    } else {
+        if (p.nsite <= 4) launch_cm<T, 3, 4>(p, s);
+        else if (p.nsite <= 8) launch_cm<T, 3, 8>(p, s);
+        else launch_cm<T, 3, 16>(p, s);
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// displacive (Taylor) recombination
+// ------------------------------------------------------------------------------------------
+// CTA: KT consecutive k (one warp each) x a chunk of 32*ZPT zones of each k's own zone box.
+// The transforms M_mu,t(k) of a chunk of TC monomials are staged in shared memory and read by
+// all lanes of a warp at once; each lane keeps the scaled coefficients
+// (Qx/Qs)^a (Qy/Qs)^b (Qz/Qs)^c of its ZPT voxels, updated with one multiply per monomial
+// (monomials run in lexicographic (a, b, c) order), and accumulates S_mu += coef * M_mu,t.
+
+constexpr int DISP_KT = 4;
+constexpr int DISP_TC = 32;
+enum { OP_MULZ = 0, OP_NEWB = 1, OP_NEWA = 2, OP_INIT = 3 };
+
+struct ZoneBox {
+    int lo[3], n[3];
+};
+
+__device__ __forceinline__ ZoneBox zone_box(const Geometry &g, const GridMap &gm, int k1, int k2, int k3) {
+    ZoneBox b;
+    const int kk[3] = {k1, k2, k3};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const int lo = ceil_div(gm.g0[a] - kk[a], g.n[a]);
+        const int hi = floor_div(gm.g0[a] + gm.cnt[a] - 1 - kk[a], g.n[a]);
+        b.lo[a] = lo;
+        b.n[a] = max(0, hi - lo + 1);
+    }
+    return b;
+}
+
+template <typename T, int MAXS, int ZPT>
+__global__ void __launch_bounds__(DISP_KT * 32) k_recomb_disp(RecombParams<T> p) {
+    using C = c_t<T>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const Geometry &g = p.g;
+    const GridMap &gm = p.gm;
+    const int nsite = p.nsite, nT = p.nT;
+    C *tile = (C *)smem_raw;                                      // [KT][nsite][TC]
+    int *ops_s = (int *)(tile + (size_t)DISP_KT * nsite * DISP_TC);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int k = blockIdx.x * DISP_KT + warp;
+    const bool kvalid = k < g.ncell;
+    const int kq = kvalid ? k : 0;
+    const int k3 = kq % g.n[2], k2 = (kq / g.n[2]) % g.n[1], k1 = kq / (g.n[2] * g.n[1]);
+    const ZoneBox zb = zone_box(g, gm, k1, k2, k3);
+    const int nzk = kvalid ? zb.n[0] * zb.n[1] * zb.n[2] : 0;
+    const int zbase = blockIdx.y * (32 * ZPT);
+
+    T qx[ZPT], qy[ZPT], qz[ZPT], ca[ZPT], cb[ZPT], cc[ZPT];
+    int Gz[ZPT][3];
+#pragma unroll
+    for (int j = 0; j < ZPT; ++j) {
+        int z = zbase + lane + 32 * j;
+        if (z >= nzk) z = 0;  // computed but never stored
+        const int nz23 = max(1, zb.n[1] * zb.n[2]);
+        const int i1 = z / nz23, rem = z - i1 * nz23;
+        const int i2 = rem / max(1, zb.n[2]), i3 = rem - i2 * max(1, zb.n[2]);
+        Gz[j][0] = g.n[0] * (zb.lo[0] + i1) + k1;
+        Gz[j][1] = g.n[1] * (zb.lo[1] + i2) + k2;
+        Gz[j][2] = g.n[2] * (zb.lo[2] + i3) + k3;
+        double Qd[3];
+        q_of_G(p.recip, g.n, Gz[j][0], Gz[j][1], Gz[j][2], Qd);
+        qx[j] = (T)(Qd[0] / p.qscale);
+        qy[j] = (T)(Qd[1] / p.qscale);
+        qz[j] = (T)(Qd[2] / p.qscale);
+        ca[j] = cb[j] = cc[j] = T(1);
+    }
+    C S[ZPT][MAXS];
+#pragma unroll
+    for (int j = 0; j < ZPT; ++j)
+#pragma unroll
+        for (int s = 0; s < MAXS; ++s) S[j][s] = mk<T>(T(0), T(0));
+
+    const bool active = zbase < nzk;  // warp-uniform
+    for (int t0 = 0; t0 < nT; t0 += DISP_TC) {
+        const int tc = min(DISP_TC, nT - t0);
+        __syncthreads();
+        for (int idx = threadIdx.x; idx < DISP_KT * nsite * tc; idx += blockDim.x) {
+            const int kk = idx % DISP_KT;
+            const int rest = idx / DISP_KT;
+            const int tt = rest % tc, s = rest / tc;
+            const int kf = blockIdx.x * DISP_KT + kk;
+            C v = mk<T>(T(0), T(0));
+            if (kf < g.ncell) {
+                const int f3 = kf % g.n[2], f2 = (kf / g.n[2]) % g.n[1], f1 = kf / (g.n[2] * g.n[1]);
+                int cj;
+                const int ki = half_index(g, f1, f2, f3, cj);
+                const int site = p.site_of[s];
+                v = p.spec[(((size_t)p.model * nsite + site) * nT + t0 + tt) * g.ncell_h + ki];
+                if (cj) v = cconj(v);
+            }
+            tile[((size_t)kk * nsite + s) * DISP_TC + tt] = v;
+        }
+        for (int tt = threadIdx.x; tt < tc; tt += blockDim.x) ops_s[tt] = p.ops[t0 + tt];
+        __syncthreads();
+        if (!active) continue;
+        const C *wt = tile + (size_t)warp * nsite * DISP_TC;
+        for (int tt = 0; tt < tc; ++tt) {
+            const int op = ops_s[tt];
+#pragma unroll
+            for (int j = 0; j < ZPT; ++j) {
+                if (op == OP_MULZ) {
+                    cc[j] *= qz[j];
+                } else if (op == OP_NEWB) {
+                    cb[j] *= qy[j];
+                    cc[j] = cb[j];
+                } else if (op == OP_NEWA) {
+                    ca[j] *= qx[j];
+                    cb[j] = ca[j];
+                    cc[j] = ca[j];
+                } else {
+                    ca[j] = cb[j] = cc[j] = T(1);
+                }
+            }
+#pragma unroll
+            for (int s = 0; s < MAXS; ++s) {
+                if (s < nsite) {
+                    const C m = wt[(size_t)s * DISP_TC + tt];
+#pragma unroll
+                    for (int j = 0; j < ZPT; ++j) {
+                        S[j][s].x = fma(cc[j], m.x, S[j][s].x);
+                        S[j][s].y = fma(cc[j], m.y, S[j][s].y);
+                    }
+                }
+            }
+        }
+    }
+    if (!active) return;
+
+    // epilogue: F = sum_mu b f(|G|) exp(iG.r_mu) S_mu, minus <F(H)> at k = 0, I = |F|^2 norm
+#pragma unroll
+    for (int j = 0; j < ZPT; ++j) {
+        const int z = zbase + lane + 32 * j;
+        if (z >= nzk) continue;
+        const int G1 = Gz[j][0], G2 = Gz[j][1], G3 = Gz[j][2];
+        const T q2 = (T)(p.qscale * p.qscale) * (qx[j] * qx[j] + qy[j] * qy[j] + qz[j] * qz[j]);
+        const T s2 = q2 * (T)(1.0 / (FOUR_PI_D * FOUR_PI_D));
+        const int H1 = (G1 - k1) / g.n[0], H2 = (G2 - k2) / g.n[1], H3 = (G3 - k3) / g.n[2];
+        const int h1 = H1 - gm.Hmin[0], h2 = H2 - gm.Hmin[1], h3 = H3 - gm.Hmin[2];
+        C F = mk<T>(T(0), T(0)), part = mk<T>(T(0), T(0));
+        int cls = 0;
+#pragma unroll
+        for (int s = 0; s < MAXS; ++s) {
+            if (s < nsite) {
+                const int site = p.site_of[s];
+                const C *tH = p.phH + (size_t)site * 3 * p.nHmax;
+                const C *tk = p.phk + (size_t)site * 3 * p.nmax;
+                C ph = cmul(cmul(tH[h1], tH[p.nHmax + h2]), tH[2 * p.nHmax + h3]);
+                ph = cmul(ph, cmul(cmul(tk[k1], tk[p.nmax + k2]), tk[2 * p.nmax + k3]));
+                ph = cscale(ph, p.scat[site]);
+                cfma(part, ph, S[j][s]);
+                if (s + 1 == p.ff.cls_end[cls]) {
+                    const T f = form_factor<T>(p.ff.cls_kind[cls], p.ff.cls_coef[cls], s2);
+                    F.x = fma(f, part.x, F.x);
+                    F.y = fma(f, part.y, F.y);
+                    part = mk<T>(T(0), T(0));
+                    ++cls;
+                }
+            }
+        }
+        if (p.diffuse && k1 == 0 && k2 == 0 && k3 == 0) {
+            const C b = p.bragg[((size_t)h1 * gm.nH[1] + h2) * gm.nH[2] + h3];
+            F = csub(F, b);
+        }
+        const T I = F.x * F.x + F.y * F.y;
+        const size_t v = ((size_t)(G1 - gm.g0[0]) * gm.cnt[1] + (G2 - gm.g0[1])) * gm.cnt[2] + (G3 - gm.g0[2]);
+        const T val = p.norm * I;
+        p.out[v] = p.accumulate ? p.out[v] + val : val;
+    }
+}
+
+template <typename T, int MAXS, int ZPT> static void launch_disp(const RecombParams<T> &p, cudaStream_t s) {
+    using C = c_t<T>;
+    // the largest per-k zone box bounds the zone chunks
+    int nzmax = 1;
+    for (int a = 0; a < 3; ++a) nzmax *= (p.gm.cnt[a] + p.g.n[a] - 1) / p.g.n[a] + 1;
+    dim3 grid((p.g.ncell + DISP_KT - 1) / DISP_KT, (nzmax + 32 * ZPT - 1) / (32 * ZPT));
+    const size_t sm = (size_t)DISP_KT * p.nsite * DISP_TC * sizeof(C) + DISP_TC * sizeof(int);
+    if (sm > 48 * 1024)
+        cudaFuncSetAttribute(k_recomb_disp<T, MAXS, ZPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_recomb_disp<T, MAXS, ZPT><<<grid, DISP_KT * 32, sm, s>>>(p);
+    count_launches(1);
+}
+
+template <typename T> void recombine_disp(const RecombParams<T> &p, cudaStream_t s) {
+    constexpr bool dbl = sizeof(T) == 8;
+    if (p.nsite <= 4) launch_disp<T, 4, dbl ? 4 : 8>(p, s);
+    else if (p.nsite <= 8) launch_disp<T, 8, dbl ? 2 : 4>(p, s);
+    else launch_disp<T, 16, dbl ? 1 : 2>(p, s);
+}
+
+// <F(H)> of Eq. bragg_sf_disp: even orders of the k = 0 transforms averaged over supercells
+template <typename T>
+__global__ void k_avg0(int nmodels, int nsite, int nT, int ncell_h, const int4 *terms, const c_t<T> *spec,
+                       c_t<T> *avg0) {
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= nsite * nT) return;
+    const int t = idx % nT;
+    c_t<T> acc = mk<T>(T(0), T(0));
+    if ((terms[t].w & 1) == 0)
+        for (int m = 0; m < nmodels; ++m) acc = cadd(acc, spec[((size_t)m * nsite * nT + idx) * ncell_h]);
+    avg0[idx] = cscale(acc, T(1) / T(nmodels));
+}
+
+template <typename T>
+__global__ void k_bragg_disp(RecombParams<T> p, const c_t<T> *avg0, c_t<T> *bragg_out) {
+    using C = c_t<T>;
+    const GridMap &gm = p.gm;
+    const int nz = gm.nH[0] * gm.nH[1] * gm.nH[2];
+    const int z = blockIdx.x * blockDim.x + threadIdx.x;
+    if (z >= nz) return;
+    const int h3 = z % gm.nH[2], h2 = (z / gm.nH[2]) % gm.nH[1], h1 = z / (gm.nH[2] * gm.nH[1]);
+    const int G1 = p.g.n[0] * (gm.Hmin[0] + h1), G2 = p.g.n[1] * (gm.Hmin[1] + h2), G3 = p.g.n[2] * (gm.Hmin[2] + h3);
+    double Qd[3];
+    q_of_G(p.recip, p.g.n, G1, G2, G3, Qd);
+    const double qx = Qd[0] / p.qscale, qy = Qd[1] / p.qscale, qz = Qd[2] / p.qscale;
+    const T q2 = (T)(Qd[0] * Qd[0] + Qd[1] * Qd[1] + Qd[2] * Qd[2]);
+    const T s2 = q2 * (T)(1.0 / (FOUR_PI_D * FOUR_PI_D));
+    C F = mk<T>(T(0), T(0)), part = mk<T>(T(0), T(0));
+    int cls = 0;
+    for (int s = 0; s < p.nsite; ++s) {
+        const int site = p.site_of[s];
+        double ca = 1, cb = 1, cc = 1;
+        C S = mk<T>(T(0), T(0));
+        for (int t = 0; t < p.nT; ++t) {
+            const int op = p.ops[t];
+            if (op == OP_MULZ) cc *= qz;
+            else if (op == OP_NEWB) { cb *= qy; cc = cb; }
+            else if (op == OP_NEWA) { ca *= qx; cb = ca; cc = ca; }
+            else { ca = cb = cc = 1; }
+            const C m = avg0[(size_t)site * p.nT + t];
+            S.x += (T)cc * m.x;
+            S.y += (T)cc * m.y;
+        }
+        const C *tH = p.phH + (size_t)site * 3 * p.nHmax;
+        C ph = cmul(cmul(tH[h1], tH[p.nHmax + h2]), tH[2 * p.nHmax + h3]);
+        ph = cscale(ph, p.scat[site]);
+        part = cadd(part, cmul(ph, S));
+        if (s + 1 == p.ff.cls_end[cls]) {
+            const T f = form_factor<T>(p.ff.cls_kind[cls], p.ff.cls_coef[cls], s2);
+            F = cadd(F, cscale(part, f));
+            part = mk<T>(T(0), T(0));
+            ++cls;
+        }
+    }
+    bragg_out[z] = F;
+}
+
+template <typename T>
+void displacive_bragg(const RecombParams<T> &p, const int4 *terms, c_t<T> *avg0, c_t<T> *bragg, cudaStream_t s) {
+    const int n0 = p.nsite * p.nT;
+    k_avg0<T><<<(n0 + 255) / 256, 256, 0, s>>>(p.nmodels, p.nsite, p.nT, p.g.ncell_h, terms, p.spec, avg0);
+    const int nz = p.gm.nH[0] * p.gm.nH[1] * p.gm.nH[2];
+    k_bragg_disp<T><<<(nz + 127) / 128, 128, 0, s>>>(p, avg0, bragg);
+    count_launches(2);
+}
+
+#define DS_INST(T)                                                                                          \
+    template void make_site_tables<T>(const Geometry &, const GridMap &, int, const double *, c_t<T> *,     \
+                                      c_t<T> *, int, int, cudaStream_t);                                    \
+    template void make_powers<T>(const Geometry &, int, int, int, double, const float *, T *, cudaStream_t); \
+    template void recombine_cm<T>(const RecombParams<T> &, cudaStream_t);                                   \
+    template void recombine_disp<T>(const RecombParams<T> &, cudaStream_t);                                 \
+    template void displacive_bragg<T>(const RecombParams<T> &, const int4 *, c_t<T> *, c_t<T> *, cudaStream_t);
+DS_INST(float)
+DS_INST(double)
+
+}  // namespace ds

@@ -1,0 +1,190 @@
+"""GPU path vs the CPU FP64 oracle, element by element, through the C boundary.
+
+Tolerances (max |I_gpu - I_oracle| / max |I_oracle|): 1e-10 for the FP64 path, 1e-5 for the
+FP32 path.  The displacive path additionally differs from the exact direct sum by at most the
+Taylor remainder bound of Section III C.
+"""
+import numpy as np
+import pytest
+
+import synthetic as syn
+from oracle import core, noise
+from _helpers import TOL, qgrid_tuple, rel_err_of_peak, to_library
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import paper_1809_07088_gb300 as ds
+    c = ds.Context(0)
+    yield c
+    c.close()
+
+
+def _G(m):
+    return m.qgrid.g_index(m.cells)
+
+
+PREC = [(0, "fp64"), (1, "fp32")]
+
+
+@pytest.mark.parametrize("prec,tag", PREC)
+@pytest.mark.parametrize("mode", [0, 1])
+def test_occupancy_small_triclinic(ctx, prec, tag, mode):
+    m = syn.small_case(syn.OCC, cells=(6, 5, 4), nsite=3, nmodels=2, seed=101)
+    lm = to_library(ctx, m)
+    got, info = lm.intensity(qgrid_tuple(m.qgrid), disorder=0, mode=mode, precision=prec)
+    want = core.occupancy_intensity_fft(m, _G(m), mode)
+    assert rel_err_of_peak(got, want) < TOL[tag]
+    direct = core.occupancy_intensity_direct(m, m.qgrid.hkl(), mode)
+    assert rel_err_of_peak(got, direct) < TOL[tag]
+    assert info["nvox"] == m.qgrid.nvox
+
+
+@pytest.mark.parametrize("prec,tag", PREC)
+@pytest.mark.parametrize("mode", [0, 1])
+def test_magnetic_small_triclinic(ctx, prec, tag, mode):
+    m = syn.small_case(syn.SPIN, cells=(5, 6, 6), nsite=4, nmodels=2, seed=102)
+    assert np.any(np.all(_G(m) == 0, axis=1))       # includes Q = 0
+    lm = to_library(ctx, m)
+    got, _ = lm.intensity(qgrid_tuple(m.qgrid), disorder=1, mode=mode, precision=prec)
+    want = core.magnetic_intensity_fft(m, _G(m), mode)
+    assert rel_err_of_peak(got, want) < TOL[tag]
+
+
+@pytest.mark.parametrize("prec,tag", PREC)
+@pytest.mark.parametrize("mode", [0, 1])
+def test_displacive_small_with_occupancy(ctx, prec, tag, mode):
+    m = syn.small_case(syn.DISP, cells=(4, 6, 5), nsite=3, nmodels=2, seed=103, sigma=0.05)
+    lm = to_library(ctx, m)
+    P = 7
+    got, info = lm.intensity(qgrid_tuple(m.qgrid), disorder=2, mode=mode, precision=prec, taylor_order=P)
+    assert info["taylor_order"] == P and info["n_monomials"] == (P + 1) * (P + 2) * (P + 3) // 6
+    want = core.displacive_intensity_fft(m, _G(m), mode, P=P)
+    assert rel_err_of_peak(got, want) < TOL[tag]
+    hkl = m.qgrid.hkl()
+    I_dir, F = core.displacive_intensity_direct(m, hkl, mode, return_F=True)
+    bound = core.truncation_bound(m, hkl, P, mode, F=F)
+    peak = np.max(np.abs(I_dir))
+    assert np.all(np.abs(got.reshape(-1) - I_dir) <= bound + 2 * TOL[tag] * peak)
+
+
+@pytest.mark.parametrize("cells", [(7, 9, 10), (12, 5, 8), (3, 14, 6), (16, 16, 16), (1, 1, 2), (2, 3, 1)])
+def test_fft_sizes_all_radices(ctx, cells):
+    """Supercells with factors 2, 3, 4, 5, 7 and degenerate axes, FP64 parity."""
+    m = syn.small_case(syn.OCC, cells=cells, nsite=2, nmodels=1, seed=104)
+    lm = to_library(ctx, m)
+    got, _ = lm.intensity(qgrid_tuple(m.qgrid), disorder=0, mode=0, precision=0)
+    want = core.occupancy_intensity_fft(m, _G(m), 0)
+    assert rel_err_of_peak(got, want) < TOL["fp64"]
+
+
+def test_single_voxel_and_single_zone_grids(ctx):
+    m = syn.small_case(syn.SPIN, cells=(4, 4, 4), nsite=2, nmodels=1, seed=105)
+    lm = to_library(ctx, m)
+    for q in [syn.QGrid((0.25, -0.5, 1.0), (0.25,) * 3, (1, 1, 1)),
+              syn.QGrid((1.0, 2.0, -1.0), (0.25,) * 3, (4, 4, 4)),
+              syn.QGrid((0.0, 0.0, 0.0), (0.25,) * 3, (1, 1, 1))]:
+        got, _ = lm.intensity(qgrid_tuple(q), disorder=1, mode=0, precision=0)
+        want = core.magnetic_intensity_fft(m, q.g_index(m.cells), 0)
+        assert rel_err_of_peak(got, want) < TOL["fp64"]
+
+
+@pytest.mark.parametrize("m_,mp", [(2, 2), (3, 2), (2, 4)])
+def test_lanczos_commensurate(ctx, m_, mp):
+    """Section V B on the commensurate grid: GPU stencil vs the literal finite sum of Eq.
+    intensity_convol_finite, with I(G) from the oracle's FFT method (halo included)."""
+    m = syn.small_case(syn.OCC, cells=(6, 5, 4), nsite=3, nmodels=1, seed=106)
+    lm = to_library(ctx, m)
+    for prec, tag in PREC:
+        got, _ = lm.intensity(qgrid_tuple(m.qgrid), disorder=0, mode=1, precision=prec, smoothing=1,
+                              lanczos_m=m_, lanczos_mprime=mp)
+        IG = lambda G: core.occupancy_intensity_fft(m, G, 1)
+        want = noise.lanczos_resample(IG, _G(m).astype(np.float64), m_, mp)
+        assert rel_err_of_peak(got, want) < TOL[tag]
+
+
+def test_device_output_on_torch_stream(ctx):
+    import torch
+    m = syn.small_case(syn.OCC, cells=(6, 5, 4), nsite=3, nmodels=1, seed=107)
+    lm = to_library(ctx, m)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        out = torch.empty(m.qgrid.count, dtype=torch.float32, device="cuda")
+        lm.intensity(qgrid_tuple(m.qgrid), out=out, disorder=0, mode=1, precision=1)
+    s.synchronize()
+    want = core.occupancy_intensity_fft(m, _G(m), 1)
+    assert rel_err_of_peak(out.cpu().numpy(), want) < TOL["fp32"]
+
+
+def test_errors_are_reported(ctx):
+    import paper_1809_07088_gb300 as ds
+    m = syn.small_case(syn.OCC, cells=(4, 4, 4), nsite=2, nmodels=1, seed=108)
+    lm = to_library(ctx, m)
+    bad = syn.QGrid((0.0, 0.0, 0.0), (0.3, 0.25, 0.25), (3, 3, 3))
+    with pytest.raises(ds.DSError) as e:
+        lm.intensity(qgrid_tuple(bad), disorder=0)
+    assert "DS_ERR_UNSUPPORTED" in str(e.value) and "commensurate" in str(e.value)
+    with pytest.raises(ds.DSError) as e:
+        lm.intensity(qgrid_tuple(m.qgrid), disorder=2)
+    assert "DS_ERR_STATE" in str(e.value)
+
+
+# ----------------------------------------------------------------------------------------------
+# the workloads at full size
+# ----------------------------------------------------------------------------------------------
+
+def test_displacive_fcc_8cubed_fp64_full_volume(ctx):
+    """fcc 8^3, sigma = 0.1 A, 64^3 voxels, FP64, Taylor order chosen by the remainder bound:
+    the whole volume against the exact direct sum within the bound, and a voxel sample
+    against the oracle's own Taylor FFT method at the same order."""
+    m = syn.displacive_fcc()
+    lm = to_library(ctx, m)
+    got, info = lm.intensity(qgrid_tuple(m.qgrid), disorder=2, mode=1, precision=0, taylor_order=-1,
+                             taylor_eps=1e-8)
+    xm = core.x_max(m, m.qgrid)
+    assert abs(info["x_max"] - xm) < 1e-9 * xm
+    P = info["taylor_order"]
+    assert P == core.taylor_order(xm, 1e-8)
+    hkl = m.qgrid.hkl()
+    I_dir, F = core.displacive_intensity_direct(m, hkl, 1, return_F=True)
+    bound = core.truncation_bound(m, hkl, P, 1, F=F)
+    peak = np.max(I_dir)
+    assert np.all(np.abs(got.reshape(-1) - I_dir) <= bound + 1e-10 * peak)
+    rng = np.random.default_rng(0)
+    G = _G(m)
+    idx = np.concatenate([rng.choice(G.shape[0], 600, replace=False),
+                          np.nonzero(np.all(np.mod(G, 8) == 0, axis=1))[0][:40]])
+    want = core.displacive_intensity_fft(m, G[idx], 1, P=P)
+    assert rel_err_of_peak(got.reshape(-1)[idx], want) < TOL["fp64"]
+
+
+def test_pyrochlore_occ_mag_20cubed(ctx):
+    """16 pyrochlore sites, 20^3 cells, 241^3 voxels (the benchmark workload): FP32 within
+    1e-5 of peak of the FP64 GPU path; FP64 within 1e-10 of the oracle on whole zones and on
+    random voxels (direct sum)."""
+    m = syn.pyrochlore_occ_mag()
+    mm = syn.magnetic_view(m)
+    lm_n = to_library(ctx, m, with_spins=False)
+    lm_m = to_library(ctx, mm)
+    q = qgrid_tuple(m.qgrid)
+    G = _G(m)
+    rng = np.random.default_rng(1)
+    idx = rng.choice(G.shape[0], 3000, replace=False)
+    H = np.floor_divide(G, 20)
+    zone = np.nonzero(np.all(H == [1, -2, 0], axis=1) | np.all(H == [-6, 5, 3], axis=1))[0]
+    for lm, model, dis, mode, fft in [(lm_n, m, 0, 1, core.occupancy_intensity_fft),
+                                      (lm_m, mm, 1, 0, core.magnetic_intensity_fft)]:
+        I64, _ = lm.intensity(q, disorder=dis, mode=mode, precision=0)
+        I32, _ = lm.intensity(q, disorder=dis, mode=mode, precision=1)
+        assert rel_err_of_peak(I32, I64) < 1e-5
+        I64f = I64.reshape(-1)
+        peak = np.max(I64f)
+        want_z = fft(model, G[zone], mode)
+        assert np.max(np.abs(I64f[zone] - want_z)) < 1e-10 * peak
+        if dis == 0:
+            want_d = core.occupancy_intensity_direct(model, G[idx] / 20.0, mode)
+        else:
+            want_d = core.magnetic_intensity_direct(model, G[idx] / 20.0, mode)
+        assert np.max(np.abs(I64f[idx] - want_d)) < 1e-10 * peak
