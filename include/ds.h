@@ -16,7 +16,7 @@
  *  - The caller owns every buffer it passes.  Uploads are copied into library-owned device
  *    memory before the call returns (host sources) or in stream order (device sources).
  *  - "is_device" flags say whether a pointer is a CUDA device pointer (1) or host memory (0).
- *  - Streams are cudaStream_t passed as void* (NULL = the library's own stream).
+ *  - Streams are cudaStream_t passed as void* (NULL = the CUDA default stream).
  *  - Cartesian frame: a along x, b in the xy plane, c with positive z.  Spins in Bohr
  *    magnetons, displacements in Angstrom, wavevectors in 1/Angstrom including 2 pi.
  *  - Arrays are C order.  Occupancy: uint8 [model][site][n1][n2][n3] (1 = occupied).

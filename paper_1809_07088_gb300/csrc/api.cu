@@ -261,7 +261,7 @@ extern "C" ds_status ds_destroy(ds_ctx *ctx) {
     if (!ctx) return DS_ERR_ARG;
     serving_shutdown(ctx);
     cudaSetDevice(ctx->device);
-    cudaStreamSynchronize(ctx->stream);
+    cudaDeviceSynchronize();
     for (ds_model *m : std::vector<ds_model *>(ctx->models.begin(), ctx->models.end())) ds_model_destroy(m);
     cudaStreamDestroy(ctx->stream);
     delete ctx;
@@ -284,7 +284,7 @@ extern "C" ds_status ds_model_create(ds_ctx *ctx, ds_model **out) {
 
 static void free_arrays(ds_model *m) {
     cudaSetDevice(m->ctx->device);
-    cudaStreamSynchronize(m->ctx->stream);
+    cudaDeviceSynchronize();
     if (m->d_occ) cudaFree(m->d_occ);
     if (m->d_spins) cudaFree(m->d_spins);
     if (m->d_disp) cudaFree(m->d_disp);
@@ -293,9 +293,36 @@ static void free_arrays(ds_model *m) {
     m->d_disp = nullptr;
 }
 
+static void free_constants(ds_model *m) {
+    cudaSetDevice(m->ctx->device);
+    cudaDeviceSynchronize();
+    for (void *p : {(void *)m->d_site_of, (void *)m->d_scat32, (void *)m->d_scat64, (void *)m->d_user_mean})
+        if (p) cudaFree(p);
+    m->d_site_of = nullptr;
+    m->d_scat32 = nullptr;
+    m->d_scat64 = nullptr;
+    m->d_user_mean = nullptr;
+    for (auto &kv : m->taylor_tables) {
+        cudaFree(kv.second.first);
+        cudaFree(kv.second.second);
+    }
+    m->taylor_tables.clear();
+}
+
+static void free_twiddles(ds_model *m) {
+    for (int a = 0; a < 3; ++a) {
+        if (m->d_tw32[a]) cudaFree(m->d_tw32[a]);
+        if (m->d_tw64[a]) cudaFree(m->d_tw64[a]);
+        m->d_tw32[a] = nullptr;
+        m->d_tw64[a] = nullptr;
+    }
+}
+
 extern "C" ds_status ds_model_destroy(ds_model *m) {
     if (!m) return DS_ERR_ARG;
     free_arrays(m);
+    free_constants(m);
+    free_twiddles(m);
     if (m->d_sites) cudaFree(m->d_sites);
     m->ctx->models.erase(m);
     delete m;
@@ -342,8 +369,40 @@ extern "C" ds_status ds_model_set_sites(ds_model *m, int nsite, const double *xy
     cudaSetDevice(ctx->device);
     if (m->d_sites) cudaFree(m->d_sites);
     m->d_sites = nullptr;
+    free_constants(m);
     CK(cudaMalloc(&m->d_sites, sizeof(double) * 3 * nsite));
     CK(cudaMemcpy(m->d_sites, xyz, sizeof(double) * 3 * nsite, cudaMemcpyHostToDevice));
+    m->ff_ok = form_factor_classes<float>(m, m->site_of, m->ff32) && form_factor_classes<double>(m, m->site_of, m->ff64);
+    std::vector<float> s32(nsite);
+    for (int i = 0; i < nsite; ++i) s32[i] = (float)m->scat[i];
+    CK(cudaMalloc(&m->d_site_of, sizeof(int) * nsite));
+    CK(cudaMalloc(&m->d_scat32, sizeof(float) * nsite));
+    CK(cudaMalloc(&m->d_scat64, sizeof(double) * nsite));
+    CK(cudaMemcpy(m->d_site_of, m->site_of.data(), sizeof(int) * nsite, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(m->d_scat32, s32.data(), sizeof(float) * nsite, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(m->d_scat64, m->scat.data(), sizeof(double) * nsite, cudaMemcpyHostToDevice));
+    return DS_OK;
+}
+
+// monomial tables of order P on the device, built once per model and order
+static ds_status taylor_tables(ds_model *m, int P, int4 **terms, int **ops, int *T) {
+    ds_ctx *ctx = m->ctx;
+    std::vector<int4> t;
+    std::vector<int> o;
+    monomial_tables(P, t, o);
+    *T = (int)t.size();
+    auto it = m->taylor_tables.find(P);
+    if (it == m->taylor_tables.end()) {
+        int4 *dt = nullptr;
+        int *dop = nullptr;
+        CK(cudaMalloc(&dt, sizeof(int4) * t.size()));
+        CK(cudaMalloc(&dop, sizeof(int) * o.size()));
+        CK(cudaMemcpy(dt, t.data(), sizeof(int4) * t.size(), cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(dop, o.data(), sizeof(int) * o.size(), cudaMemcpyHostToDevice));
+        it = m->taylor_tables.emplace(P, std::make_pair(dt, dop)).first;
+    }
+    *terms = it->second.first;
+    *ops = it->second.second;
     return DS_OK;
 }
 
@@ -357,11 +416,20 @@ extern "C" ds_status ds_model_set_supercell(ds_model *m, int n1, int n2, int n3,
         return ds_fail(ctx, DS_ERR_UNSUPPORTED, "supercell %dx%dx%d: each n must be 1..128 with prime factors 2,3,5,7",
                        n1, n2, n3);
     free_arrays(m);
+    free_twiddles(m);
     m->has_occ = m->has_spins = m->has_disp = false;
     m->n[0] = n1;
     m->n[1] = n2;
     m->n[2] = n3;
     m->nmodels = nmodels;
+    cudaSetDevice(ctx->device);
+    for (int a = 0; a < 3; ++a) {
+        CK(cudaMalloc(&m->d_tw32[a], sizeof(c_t<float>) * n[a]));
+        CK(cudaMalloc(&m->d_tw64[a], sizeof(c_t<double>) * n[a]));
+        make_twiddles<float>(n[a], m->d_tw32[a], 0);
+        make_twiddles<double>(n[a], m->d_tw64[a], 0);
+    }
+    CK(cudaDeviceSynchronize());
     m->has_cells = true;
     return DS_OK;
 }
@@ -371,7 +439,7 @@ static ds_status upload(ds_model *m, void **dst, const void *src, size_t bytes, 
     if (!src) return ds_fail(ctx, DS_ERR_ARG, "null source array");
     if (!m->has_cells || m->nsite < 1) return ds_fail(ctx, DS_ERR_STATE, "set sites and supercell first");
     cudaSetDevice(ctx->device);
-    cudaStream_t st = stream ? (cudaStream_t)stream : ctx->stream;
+    cudaStream_t st = (cudaStream_t)stream;
     if (!*dst) CK(cudaMalloc(dst, bytes));
     CK(cudaMemcpyAsync(*dst, src, bytes, src_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
     if (!src_dev) CK(cudaStreamSynchronize(st));
@@ -387,7 +455,12 @@ extern "C" ds_status ds_model_upload_occupancy(ds_model *m, const uint8_t *occ, 
     if (st != DS_OK) return st;
     m->has_occ = true;
     m->user_mean = mean != nullptr;
-    if (mean) m->mean_occ.assign(mean, mean + m->nsite);
+    if (mean) {
+        ds_ctx *ctx = m->ctx;
+        m->mean_occ.assign(mean, mean + m->nsite);
+        if (!m->d_user_mean) CK(cudaMalloc(&m->d_user_mean, sizeof(double) * m->nsite));
+        CK(cudaMemcpy(m->d_user_mean, mean, sizeof(double) * m->nsite, cudaMemcpyHostToDevice));
+    }
     return DS_OK;
 }
 
@@ -487,35 +560,32 @@ ds_status plan_and_run(ds_model *M, const ds_qgrid *q, const ds_opts *o, T *d_ou
     p.nsite = nsite;
     p.nmodels = nmod;
     p.diffuse = o->mode == DS_DIFFUSE;
-    std::vector<int> site_of;
-    if (!form_factor_classes<T>(M, site_of, p.ff))
-        return ds_fail(ctx, DS_ERR_UNSUPPORTED, "more than %d distinct form factors", MAX_FF_CLASSES);
+    if (!M->ff_ok) return ds_fail(ctx, DS_ERR_UNSUPPORTED, "more than %d distinct form factors", MAX_FF_CLASSES);
+    if constexpr (sizeof(T) == 4) p.ff = M->ff32;
+    else p.ff = M->ff64;
     memcpy(p.recip, M->recip, sizeof(p.recip));
     const double N = (double)nsite * g.ncell;
     p.norm = (T)(1.0 / (nmod * N));
     if (o->disorder == DS_SPIN) p.norm = (T)(0.07265 / (nmod * N));  // C of Eq. mag_intensity (barn)
 
-    // small tables
+    // small tables: site phases of this grid (twiddles, site order and b are per model)
     p.nmax = std::max(g.n[0], std::max(g.n[1], g.n[2]));
     p.nHmax = std::max(gm.nH[0], std::max(gm.nH[1], gm.nH[2]));
     C *phk = (C *)ws.get(sizeof(C) * nsite * 3 * p.nmax);
     C *phH = (C *)ws.get(sizeof(C) * nsite * 3 * p.nHmax);
-    int *d_site_of = (int *)ws.get(sizeof(int) * nsite);
-    T *d_scat = (T *)ws.get(sizeof(T) * nsite);
-    C *W[3];
-    for (int a = 0; a < 3; ++a) W[a] = (C *)ws.get(sizeof(C) * g.n[a]);
     double *d_mean = (double *)ws.get(sizeof(double) * nsite * 3);
     if (ws.failed) return ds_fail(ctx, DS_ERR_OOM, "device allocation failed (tables)");
-    std::vector<T> scat(nsite);
-    for (int i = 0; i < nsite; ++i) scat[i] = (T)M->scat[i];
-    CK(cudaMemcpyAsync(d_site_of, site_of.data(), sizeof(int) * nsite, cudaMemcpyHostToDevice, st));
-    CK(cudaMemcpyAsync(d_scat, scat.data(), sizeof(T) * nsite, cudaMemcpyHostToDevice, st));
-    for (int a = 0; a < 3; ++a) make_twiddles<T>(g.n[a], W[a], st);
+    const C *W[3];
+    for (int a = 0; a < 3; ++a) {
+        if constexpr (sizeof(T) == 4) W[a] = M->d_tw32[a];
+        else W[a] = M->d_tw64[a];
+    }
     make_site_tables<T>(g, gm, nsite, M->d_sites, phk, phH, p.nmax, p.nHmax, st);
     p.phk = phk;
     p.phH = phH;
-    p.site_of = d_site_of;
-    p.scat = d_scat;
+    p.site_of = M->d_site_of;
+    if constexpr (sizeof(T) == 4) p.scat = M->d_scat32;
+    else p.scat = M->d_scat64;
     p.out = d_out;
 
     FieldSource src;
@@ -524,20 +594,16 @@ ds_status plan_and_run(ds_model *M, const ds_qgrid *q, const ds_opts *o, T *d_ou
     src.diffuse = o->mode == DS_DIFFUSE;
     int nf_model = 0;
     int P = 0, Tn = 1;
-    std::vector<int4> terms;
-    std::vector<int> ops;
     double xmax = -1.0;
     if (o->disorder == DS_OCC) {
         src.kind = SRC_OCC;
         src.occ = M->d_occ;
         nf_model = nsite;
-        if (src.diffuse) {
-            if (M->user_mean)
-                CK(cudaMemcpyAsync(d_mean, M->mean_occ.data(), sizeof(double) * nsite, cudaMemcpyHostToDevice, st));
-            else
-                site_means_occ(nmod, nsite, g.ncell, M->d_occ, d_mean, st);
-        }
         src.mean = d_mean;
+        if (src.diffuse) {
+            if (M->user_mean) src.mean = M->d_user_mean;
+            else site_means_occ(nmod, nsite, g.ncell, M->d_occ, d_mean, st);
+        }
         p.ncomp = 1;
     } else if (o->disorder == DS_SPIN) {
         src.kind = SRC_SPIN;
@@ -547,18 +613,16 @@ ds_status plan_and_run(ds_model *M, const ds_qgrid *q, const ds_opts *o, T *d_ou
         src.mean = d_mean;
         p.ncomp = 3;
     } else {
-        double corners[24];
-        box_corners(M, eg0, ecnt, corners);
+        Corners corners;
+        box_corners(M, eg0, ecnt, corners.v);
         double qscale = 0.0;
-        for (int i = 0; i < 24; ++i) qscale = std::max(qscale, fabs(corners[i]));
+        for (int i = 0; i < 24; ++i) qscale = std::max(qscale, fabs(corners.v[i]));
         if (!(qscale > 0)) qscale = 1.0;
         P = o->taylor_order;
         if (P < 0) {
-            double *d_corners = (double *)ws.get(sizeof(double) * 24);
             double *d_x = (double *)ws.get(sizeof(double) * 8);
             if (ws.failed) return ds_fail(ctx, DS_ERR_OOM, "device allocation failed");
-            CK(cudaMemcpyAsync(d_corners, corners, sizeof(corners), cudaMemcpyHostToDevice, st));
-            corner_xmax((int)natom, M->d_disp, d_corners, d_x, st);
+            corner_xmax((int)natom, M->d_disp, corners, d_x, st);
             double hx[8];
             CK(cudaMemcpyAsync(hx, d_x, sizeof(hx), cudaMemcpyDeviceToHost, st));
             CK(cudaStreamSynchronize(st));
@@ -567,14 +631,12 @@ ds_status plan_and_run(ds_model *M, const ds_qgrid *q, const ds_opts *o, T *d_ou
             P = taylor_order_for(xmax, o->taylor_eps);
             if (P < 0 || P > 60) return ds_fail(ctx, DS_ERR_UNSUPPORTED, "Taylor order above 60 (x_max = %g)", xmax);
         }
-        monomial_tables(P, terms, ops);
-        Tn = (int)terms.size();
-        int4 *d_terms = (int4 *)ws.get(sizeof(int4) * Tn);
-        int *d_ops = (int *)ws.get(sizeof(int) * Tn);
+        int4 *d_terms = nullptr;
+        int *d_ops = nullptr;
+        rc = taylor_tables(M, P, &d_terms, &d_ops, &Tn);
+        if (rc != DS_OK) return rc;
         T *pw = (T *)ws.get(sizeof(T) * natom * 3 * (P + 1));
         if (ws.failed) return ds_fail(ctx, DS_ERR_OOM, "device allocation failed (power tables)");
-        CK(cudaMemcpyAsync(d_terms, terms.data(), sizeof(int4) * Tn, cudaMemcpyHostToDevice, st));
-        CK(cudaMemcpyAsync(d_ops, ops.data(), sizeof(int) * Tn, cudaMemcpyHostToDevice, st));
         make_powers<T>(g, nmod, nsite, P, qscale, M->d_disp, pw, st);
         src.kind = SRC_DISP;
         src.pw = pw;
@@ -586,6 +648,7 @@ ds_status plan_and_run(ds_model *M, const ds_qgrid *q, const ds_opts *o, T *d_ou
         p.ncomp = 1;
         p.nT = Tn;
         p.ops = d_ops;
+        p.terms = d_terms;
         p.qscale = qscale;
         if (keep) {
             keep->terms = d_terms;
@@ -724,7 +787,7 @@ extern "C" ds_status ds_request_intensity(ds_model *M, const ds_qgrid *q, const 
     ds_status rc = check_request(M, q, o);
     if (rc != DS_OK) return rc;
     CK(cudaSetDevice(ctx->device));
-    cudaStream_t st = stream ? (cudaStream_t)stream : ctx->stream;
+    cudaStream_t st = (cudaStream_t)stream;
     if (o->precision == DS_FP64) return run_intensity<double>(M, q, o, out, out_is_device, st, info);
     return run_intensity<float>(M, q, o, out, out_is_device, st, info);
 }

@@ -34,6 +34,18 @@ struct ds_model {
     bool has_occ = false, has_spins = false, has_disp = false;
     bool user_mean = false;
     std::vector<double> mean_occ;
+    double *d_user_mean = nullptr;
+    // per-model constants of the launch sequence, built once by set_sites / set_supercell
+    bool ff_ok = false;
+    std::vector<int> site_of;             // sorted position -> site (form-factor classes contiguous)
+    ds::FormFactors<float> ff32;
+    ds::FormFactors<double> ff64;
+    int *d_site_of = nullptr;
+    float *d_scat32 = nullptr;
+    double *d_scat64 = nullptr;
+    ds::c_t<float> *d_tw32[3] = {nullptr, nullptr, nullptr};
+    ds::c_t<double> *d_tw64[3] = {nullptr, nullptr, nullptr};
+    std::map<int, std::pair<int4 *, int *>> taylor_tables;   // order P -> (terms, ops) on device
 };
 
 struct ProfRecord {

@@ -83,6 +83,7 @@ template <typename T> struct RecombParams {
     double qscale;                      // displacive: coefficient uses Q / qscale
     T norm;                             // 1/(nmodels N), times C for magnetic
     const int *ops;                     // displacive coefficient update codes per monomial
+    const int4 *terms;                  // displacive monomials (a, b, c, n)
     const c_t<T> *bragg;                // displacive DIFFUSE: <F(H)> per zone [nH1][nH2][nH3]
     T *out;                             // [cnt1][cnt2][cnt3]
     int *err;
@@ -104,8 +105,10 @@ void make_powers(const Geometry &g, int nmodels, int nsite, int P, double qscale
                  T *pw, cudaStream_t s);
 void site_means_occ(int nmodels, int nsite, int ncell, const uint8_t *occ, double *mean, cudaStream_t s);
 void site_means_spin(int nmodels, int nsite, int ncell, const float *spins, double *mean, cudaStream_t s);
-void corner_xmax(int natom, const float *disp, const double *corners /*dev [8][3]*/, double *out /*dev [8]*/,
-                 cudaStream_t s);
+struct Corners {
+    double v[24];  // 8 Cartesian Q vectors
+};
+void corner_xmax(int natom, const float *disp, const Corners &corners, double *out /*dev [8]*/, cudaStream_t s);
 template <typename T> void recombine_cm(const RecombParams<T> &p, cudaStream_t s);
 template <typename T> void recombine_disp(const RecombParams<T> &p, cudaStream_t s);
 template <typename T>

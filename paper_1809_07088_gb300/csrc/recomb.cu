@@ -126,7 +126,8 @@ void site_means_spin(int nmodels, int nsite, int ncell, const float *spins, doub
 
 // out[c] = max_j |Q_c . u_j| for the 8 corners of the Q box (non-negative doubles order like
 // their bit patterns, so an integer atomicMax is exact)
-__global__ void k_corner_xmax(int natom, const float *disp, const double *corners, unsigned long long *out) {
+__global__ void k_corner_xmax(int natom, const float *disp, const Corners cq, unsigned long long *out) {
+    const double *corners = cq.v;
     double best[8];
 #pragma unroll
     for (int c = 0; c < 8; ++c) best[c] = 0.0;
@@ -144,7 +145,7 @@ __global__ void k_corner_xmax(int natom, const float *disp, const double *corner
     }
 }
 
-void corner_xmax(int natom, const float *disp, const double *corners, double *out, cudaStream_t s) {
+void corner_xmax(int natom, const float *disp, const Corners &corners, double *out, cudaStream_t s) {
     cudaMemsetAsync(out, 0, 8 * sizeof(double), s);
     int nb = std::min(1024, std::max(1, (natom + 255) / 256));
     k_corner_xmax<<<nb, 256, 0, s>>>(natom, disp, corners, (unsigned long long *)out);
@@ -243,11 +244,19 @@ __global__ void __launch_bounds__(256) k_recomb_cm(RecombParams<T> p, int h12_pe
         if (G2 < gm.g0[1] || G2 >= gm.g0[1] + gm.cnt[1]) continue;
         const C *Prow = Ptab + (size_t)j12 * nH3 * nsite;
         const size_t vrow = ((size_t)(G1 - gm.g0[0]) * gm.cnt[1] + (G2 - gm.g0[1])) * gm.cnt[2];
+        // Cartesian Q = (G1/n1) a* + (G2/n2) b* + (G3/n3) c*, the G3 part added per voxel
+        T Q12[3], c3[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            Q12[a] = (T)((double)G1 / g.n[0] * p.recip[a] + (double)G2 / g.n[1] * p.recip[3 + a]);
+            c3[a] = (T)(p.recip[6 + a] / g.n[2]);
+        }
         for (int h3 = h3lo; h3 <= h3hi; ++h3) {
             const int G3 = g.n[2] * (gm.Hmin[2] + h3) + k3;
-            double Qd[3];
-            q_of_G(p.recip, g.n, G1, G2, G3, Qd);
-            const T q2 = (T)(Qd[0] * Qd[0] + Qd[1] * Qd[1] + Qd[2] * Qd[2]);
+            T Qd[3];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) Qd[a] = fma((T)G3, c3[a], Q12[a]);
+            const T q2 = Qd[0] * Qd[0] + Qd[1] * Qd[1] + Qd[2] * Qd[2];
             const T s2 = q2 * (T)(1.0 / (FOUR_PI_D * FOUR_PI_D));
             const C *P = Prow + (size_t)h3 * nsite;
             C F[NC], part[NC];
@@ -281,7 +290,7 @@ __global__ void __launch_bounds__(256) k_recomb_cm(RecombParams<T> p, int h12_pe
                 for (int c = 0; c < NC; ++c) tot += F[c].x * F[c].x + F[c].y * F[c].y;
                 if (q2 > T(0)) {
                     const T iq = T(1) / sqrt(q2);
-                    const T qx = (T)Qd[0] * iq, qy = (T)Qd[1] * iq, qz = (T)Qd[2] * iq;
+                    const T qx = Qd[0] * iq, qy = Qd[1] * iq, qz = Qd[2] * iq;
                     const T pr = qx * F[0].x + qy * F[1].x + qz * F[2].x;
                     const T pi = qx * F[0].y + qy * F[1].y + qz * F[2].y;
                     I = tot - (pr * pr + pi * pi);
@@ -417,7 +426,11 @@ __global__ void __launch_bounds__(DISP_KT * 32) k_recomb_disp(RecombParams<T> p)
                 const int ki = half_index(g, f1, f2, f3, cj);
                 const int site = p.site_of[s];
                 v = p.spec[(((size_t)p.model * nsite + site) * nT + t0 + tt) * g.ncell_h + ki];
-                if (cj) v = cconj(v);
+                // stored: i^n M(k) on the half spectrum; i^n M(k) = (-1)^n conj(i^n M(-k))
+                if (cj) {
+                    v = cconj(v);
+                    if (p.terms[t0 + tt].w & 1) v = mk<T>(-v.x, -v.y);
+                }
             }
             tile[((size_t)kk * nsite + s) * DISP_TC + tt] = v;
         }
