@@ -184,6 +184,14 @@ static bool form_factor_classes(const ds_model *M, std::vector<int> &site_of, Fo
         return false;
     };
     std::stable_sort(site_of.begin(), site_of.end(), key_less);
+    // within a class, order by z = r3 mod 1 so that sites sharing exp(2 pi i H3 z) are adjacent
+    auto zfrac = [&](int s) { double z = M->sites[3 * s + 2]; return z - floor(z); };
+    for (int i = 0; i < ns;) {
+        int j = i + 1;
+        while (j < ns && !key_less(site_of[i], site_of[j]) && !key_less(site_of[j], site_of[i])) ++j;
+        std::stable_sort(site_of.begin() + i, site_of.begin() + j, [&](int x, int y) { return zfrac(x) < zfrac(y); });
+        i = j;
+    }
     ff.ncls = 0;
     for (int i = 0; i < ns; ++i) {
         const bool same = i > 0 && !key_less(site_of[i - 1], site_of[i]) && !key_less(site_of[i], site_of[i - 1]);
@@ -263,6 +271,11 @@ extern "C" ds_status ds_destroy(ds_ctx *ctx) {
     cudaSetDevice(ctx->device);
     cudaDeviceSynchronize();
     for (ds_model *m : std::vector<ds_model *>(ctx->models.begin(), ctx->models.end())) ds_model_destroy(m);
+    for (auto &r : ctx->prof) {
+        cudaEventDestroy(r.e0);
+        cudaEventDestroy(r.e1);
+    }
+    for (cudaEvent_t e : ctx->event_pool) cudaEventDestroy(e);
     cudaStreamDestroy(ctx->stream);
     delete ctx;
     return DS_OK;
@@ -373,6 +386,31 @@ extern "C" ds_status ds_model_set_sites(ds_model *m, int nsite, const double *xy
     CK(cudaMalloc(&m->d_sites, sizeof(double) * 3 * nsite));
     CK(cudaMemcpy(m->d_sites, xyz, sizeof(double) * 3 * nsite, cudaMemcpyHostToDevice));
     m->ff_ok = form_factor_classes<float>(m, m->site_of, m->ff32) && form_factor_classes<double>(m, m->site_of, m->ff64);
+    if (m->ff_ok) {
+        // groups: consecutive sorted sites of one class with equal z mod 1
+        SiteGroups &G = m->groups;
+        memset(&G, 0, sizeof(G));
+        int cls = 0;
+        double zprev = -1.0;
+        for (int i = 0; i < nsite; ++i) {
+            bool boundary = i == 0;
+            if (i > 0 && i == m->ff64.cls_end[cls]) {
+                G.cls_grp_end[cls] = G.ngrp;
+                ++cls;
+                boundary = true;
+            }
+            const int s = m->site_of[i];
+            const double z = m->sites[3 * s + 2] - floor(m->sites[3 * s + 2]);
+            if (boundary || z != zprev) {
+                G.grp_site[G.ngrp] = s;
+                G.ngrp++;
+            }
+            G.grp_end[G.ngrp - 1] = i + 1;
+            zprev = z;
+        }
+        G.cls_grp_end[cls] = G.ngrp;
+        for (int c = cls + 1; c < MAX_FF_CLASSES; ++c) G.cls_grp_end[c] = -1;
+    }
     std::vector<float> s32(nsite);
     for (int i = 0; i < nsite; ++i) s32[i] = (float)m->scat[i];
     CK(cudaMalloc(&m->d_site_of, sizeof(int) * nsite));
@@ -563,6 +601,7 @@ ds_status plan_and_run(ds_model *M, const ds_qgrid *q, const ds_opts *o, T *d_ou
     if (!M->ff_ok) return ds_fail(ctx, DS_ERR_UNSUPPORTED, "more than %d distinct form factors", MAX_FF_CLASSES);
     if constexpr (sizeof(T) == 4) p.ff = M->ff32;
     else p.ff = M->ff64;
+    p.grp = M->groups;
     memcpy(p.recip, M->recip, sizeof(p.recip));
     const double N = (double)nsite * g.ncell;
     p.norm = (T)(1.0 / (nmod * N));
@@ -804,11 +843,23 @@ template ds_status plan_and_run<double>(ds_model *, const ds_qgrid *, const ds_o
 static std::atomic<long long> g_launches{0};
 void ds::count_launches(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
+static cudaEvent_t pool_event(ds_ctx *ctx) {
+    std::lock_guard<std::mutex> g(ctx->prof_mu);
+    if (ctx->event_pool.empty()) {
+        cudaEvent_t e;
+        cudaEventCreate(&e);
+        return e;
+    }
+    cudaEvent_t e = ctx->event_pool.back();
+    ctx->event_pool.pop_back();
+    return e;
+}
+
 ProfScope::ProfScope(ds_ctx *c, const char *name, cudaStream_t st) : ctx(c), s(st), on(c && c->prof_on) {
     if (!on) return;
     rec.name = name;
-    cudaEventCreate(&rec.e0);
-    cudaEventCreate(&rec.e1);
+    rec.e0 = pool_event(ctx);
+    rec.e1 = pool_event(ctx);
     cudaEventRecord(rec.e0, s);
 }
 ProfScope::~ProfScope() {
@@ -849,8 +900,13 @@ extern "C" ds_status ds_profile_report(ds_ctx *ctx, char *json, size_t cap) {
         }
         ms[i] += t;
         cnt[i] += 1;
-        cudaEventDestroy(r.e0);
-        cudaEventDestroy(r.e1);
+    }
+    {
+        std::lock_guard<std::mutex> g(ctx->prof_mu);
+        for (auto &r : recs) {
+            ctx->event_pool.push_back(r.e0);
+            ctx->event_pool.push_back(r.e1);
+        }
     }
     std::string out = "{\"stages\": {";
     for (size_t i = 0; i < names.size(); ++i) {

@@ -40,6 +40,7 @@ struct ds_model {
     std::vector<int> site_of;             // sorted position -> site (form-factor classes contiguous)
     ds::FormFactors<float> ff32;
     ds::FormFactors<double> ff64;
+    ds::SiteGroups groups;
     int *d_site_of = nullptr;
     float *d_scat32 = nullptr;
     double *d_scat64 = nullptr;
@@ -59,6 +60,7 @@ struct ds_ctx {
     bool prof_on = false;
     std::mutex prof_mu;
     std::vector<ProfRecord> prof;
+    std::vector<cudaEvent_t> event_pool;   // reused by the tracing scopes
     size_t budget = 0;
     std::mutex err_mu;
     std::string err;

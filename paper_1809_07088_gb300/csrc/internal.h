@@ -64,6 +64,15 @@ template <typename T> struct FormFactors {
     T cls_coef[MAX_FF_CLASSES][9];
 };
 
+// sites sorted by (form-factor class, z = r_mu,3 mod 1); a group = sites of one class sharing z,
+// so that exp(2 pi i H3 z) is common to the group
+struct SiteGroups {
+    int ngrp;
+    int grp_end[MAX_SITES];            // exclusive end of each group (sorted positions)
+    int grp_site[MAX_SITES];           // one site of each group (its z is the group's)
+    int cls_grp_end[MAX_FF_CLASSES];   // exclusive end of each form-factor class (group index)
+};
+
 template <typename T> struct RecombParams {
     Geometry g;
     GridMap gm;
@@ -79,6 +88,7 @@ template <typename T> struct RecombParams {
     const int *site_of;                 // sorted position -> site
     const T *scat;                      // b per site
     FormFactors<T> ff;
+    SiteGroups grp;
     double recip[9];                    // a*, b*, c* rows (1/A)
     double qscale;                      // displacive: coefficient uses Q / qscale
     T norm;                             // 1/(nmodels N), times C for magnetic

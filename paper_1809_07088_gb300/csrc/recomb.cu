@@ -177,10 +177,20 @@ __device__ __forceinline__ void q_of_G(const double *recip, const int *n, int G1
 // Y_mu,c(k) = b_mu exp(ik.r_mu) X_mu,c(k) of its k in registers and sweeps the zones, reading
 // exp(iH.r_mu) from a shared-memory table that every thread of the warp reads at once.
 
-template <typename T, int NC, int MAXS>
-__global__ void __launch_bounds__(256) k_recomb_cm(RecombParams<T> p, int h12_per_cta) {
+template <typename T> struct CmConfig {
+    int h12_per_cta;
+};
+
+// One voxel pass of the site sum for VPI consecutive h3 zones, then the epilogue.
+// ONECLS: every site shares one form factor (applied once after the site sum).
+template <typename T, int NC, int MAXS, bool ONECLS, int VPI, int MINB>
+__global__ void __launch_bounds__(256, MINB)
+    k_recomb_cm(const __grid_constant__ RecombParams<T> p, int h12_per_cta) {
     using C = c_t<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ int cls_end_s[MAX_FF_CLASSES];
+    __shared__ int cls_kind_s[MAX_FF_CLASSES];
+    __shared__ T cls_coef_s[MAX_FF_CLASSES][9];
     C *Ptab = (C *)smem_raw;
     const Geometry &g = p.g;
     const GridMap &gm = p.gm;
@@ -190,6 +200,12 @@ __global__ void __launch_bounds__(256) k_recomb_cm(RecombParams<T> p, int h12_pe
     const int nh12 = min(h12_per_cta, nH12 - h12_0);
     const int nH3 = gm.nH[2];
 
+    if (threadIdx.x < MAX_FF_CLASSES) {
+        cls_end_s[threadIdx.x] = p.ff.cls_end[threadIdx.x];
+        cls_kind_s[threadIdx.x] = p.ff.cls_kind[threadIdx.x];
+#pragma unroll
+        for (int j = 0; j < 9; ++j) cls_coef_s[threadIdx.x][j] = p.ff.cls_coef[threadIdx.x][j];
+    }
     for (int idx = threadIdx.x; idx < nh12 * nH3 * nsite; idx += blockDim.x) {
         const int s = idx % nsite;
         const int h3 = (idx / nsite) % nH3;
@@ -234,6 +250,8 @@ __global__ void __launch_bounds__(256) k_recomb_cm(RecombParams<T> p, int h12_pe
             for (int c = 0; c < NC; ++c) Y[s][c] = mk<T>(T(0), T(0));
         }
     }
+    const int kind0 = cls_kind_s[0];
+    const T inv16pi2 = (T)(1.0 / (FOUR_PI_D * FOUR_PI_D));
 
     for (int j12 = 0; j12 < nh12; ++j12) {
         const int h12 = h12_0 + j12;
@@ -243,7 +261,7 @@ __global__ void __launch_bounds__(256) k_recomb_cm(RecombParams<T> p, int h12_pe
         if (G1 < gm.g0[0] || G1 >= gm.g0[0] + gm.cnt[0]) continue;
         if (G2 < gm.g0[1] || G2 >= gm.g0[1] + gm.cnt[1]) continue;
         const C *Prow = Ptab + (size_t)j12 * nH3 * nsite;
-        const size_t vrow = ((size_t)(G1 - gm.g0[0]) * gm.cnt[1] + (G2 - gm.g0[1])) * gm.cnt[2];
+        T *orow = p.out + ((size_t)(G1 - gm.g0[0]) * gm.cnt[1] + (G2 - gm.g0[1])) * gm.cnt[2] - gm.g0[2];
         // Cartesian Q = (G1/n1) a* + (G2/n2) b* + (G3/n3) c*, the G3 part added per voxel
         T Q12[3], c3[3];
 #pragma unroll
@@ -251,77 +269,325 @@ __global__ void __launch_bounds__(256) k_recomb_cm(RecombParams<T> p, int h12_pe
             Q12[a] = (T)((double)G1 / g.n[0] * p.recip[a] + (double)G2 / g.n[1] * p.recip[3 + a]);
             c3[a] = (T)(p.recip[6 + a] / g.n[2]);
         }
-        for (int h3 = h3lo; h3 <= h3hi; ++h3) {
-            const int G3 = g.n[2] * (gm.Hmin[2] + h3) + k3;
-            T Qd[3];
+        for (int h3 = h3lo; h3 <= h3hi; h3 += VPI) {
+            C F[VPI][NC], part[VPI][NC];
 #pragma unroll
-            for (int a = 0; a < 3; ++a) Qd[a] = fma((T)G3, c3[a], Q12[a]);
-            const T q2 = Qd[0] * Qd[0] + Qd[1] * Qd[1] + Qd[2] * Qd[2];
-            const T s2 = q2 * (T)(1.0 / (FOUR_PI_D * FOUR_PI_D));
-            const C *P = Prow + (size_t)h3 * nsite;
-            C F[NC], part[NC];
+            for (int v = 0; v < VPI; ++v)
 #pragma unroll
-            for (int c = 0; c < NC; ++c) F[c] = part[c] = mk<T>(T(0), T(0));
+                for (int c = 0; c < NC; ++c) F[v][c] = part[v][c] = mk<T>(T(0), T(0));
+            T s2[VPI], Qv[VPI][3], q2[VPI];
+#pragma unroll
+            for (int v = 0; v < VPI; ++v) {
+                const int G3 = g.n[2] * (gm.Hmin[2] + min(h3 + v, h3hi)) + k3;
+#pragma unroll
+                for (int a = 0; a < 3; ++a) Qv[v][a] = fma((T)G3, c3[a], Q12[a]);
+                q2[v] = Qv[v][0] * Qv[v][0] + Qv[v][1] * Qv[v][1] + Qv[v][2] * Qv[v][2];
+                s2[v] = q2[v] * inv16pi2;
+            }
             int cls = 0;
 #pragma unroll
             for (int s = 0; s < MAXS; ++s) {
                 if (s < nsite) {
-                    const C ps = P[s];
 #pragma unroll
-                    for (int c = 0; c < NC; ++c) cfma(part[c], ps, Y[s][c]);
-                    if (s + 1 == p.ff.cls_end[cls]) {
-                        const T f = form_factor<T>(p.ff.cls_kind[cls], p.ff.cls_coef[cls], s2);
+                    for (int v = 0; v < VPI; ++v) {
+                        const C ps = Prow[(size_t)min(h3 + v, h3hi) * nsite + s];
+                        if (ONECLS) {
 #pragma unroll
-                        for (int c = 0; c < NC; ++c) {
-                            F[c].x = fma(f, part[c].x, F[c].x);
-                            F[c].y = fma(f, part[c].y, F[c].y);
-                            part[c] = mk<T>(T(0), T(0));
+                            for (int c = 0; c < NC; ++c) cfma(F[v][c], ps, Y[s][c]);
+                        } else {
+#pragma unroll
+                            for (int c = 0; c < NC; ++c) cfma(part[v][c], ps, Y[s][c]);
+                        }
+                    }
+                    if (!ONECLS && s + 1 == cls_end_s[cls]) {
+#pragma unroll
+                        for (int v = 0; v < VPI; ++v) {
+                            const T f = form_factor<T>(cls_kind_s[cls], cls_coef_s[cls], s2[v]);
+#pragma unroll
+                            for (int c = 0; c < NC; ++c) {
+                                F[v][c].x = fma(f, part[v][c].x, F[v][c].x);
+                                F[v][c].y = fma(f, part[v][c].y, F[v][c].y);
+                                part[v][c] = mk<T>(T(0), T(0));
+                            }
                         }
                         ++cls;
                     }
                 }
             }
-            T I;
-            if (NC == 1) {
-                I = F[0].x * F[0].x + F[0].y * F[0].y;
-            } else {
+#pragma unroll
+            for (int v = 0; v < VPI; ++v) {
+                if (h3 + v > h3hi) break;
                 T tot = T(0);
 #pragma unroll
-                for (int c = 0; c < NC; ++c) tot += F[c].x * F[c].x + F[c].y * F[c].y;
-                if (q2 > T(0)) {
-                    const T iq = T(1) / sqrt(q2);
-                    const T qx = Qd[0] * iq, qy = Qd[1] * iq, qz = Qd[2] * iq;
-                    const T pr = qx * F[0].x + qy * F[1].x + qz * F[2].x;
-                    const T pi = qx * F[0].y + qy * F[1].y + qz * F[2].y;
-                    I = tot - (pr * pr + pi * pi);
-                } else {
-                    I = T(2) / T(3) * tot;
+                for (int c = 0; c < NC; ++c) tot += F[v][c].x * F[v][c].x + F[v][c].y * F[v][c].y;
+                T I = tot;
+                if (NC == 3) {
+                    if (q2[v] > T(0)) {
+                        const T pr = Qv[v][0] * F[v][0].x + Qv[v][1] * F[v][1].x + Qv[v][2] * F[v][2].x;
+                        const T pi = Qv[v][0] * F[v][0].y + Qv[v][1] * F[v][1].y + Qv[v][2] * F[v][2].y;
+                        I = tot - (pr * pr + pi * pi) / q2[v];
+                    } else {
+                        I = T(2) / T(3) * tot;
+                    }
                 }
+                if (ONECLS && kind0 != 0) {
+                    const T f = form_factor<T>(kind0, cls_coef_s[0], s2[v]);
+                    I *= f * f;
+                }
+                T *dst = orow + g.n[2] * (gm.Hmin[2] + h3 + v) + k3;
+                const T val = p.norm * I;
+                *dst = p.accumulate ? *dst + val : val;
             }
-            const size_t v = vrow + (G3 - gm.g0[2]);
-            const T val = p.norm * I;
-            p.out[v] = p.accumulate ? p.out[v] + val : val;
         }
     }
 }
 
-template <typename T, int NC, int MAXS> static void launch_cm(const RecombParams<T> &p, cudaStream_t s) {
+template <typename T, int NC, int MAXS, bool ONECLS, int VPI, int MINB>
+void launch_cm_variant(const RecombParams<T> &p, int per, cudaStream_t s) {
     using C = c_t<T>;
     const int nH12 = p.gm.nH[0] * p.gm.nH[1];
     const int ktiles = (p.g.ncell + 255) / 256;
-    // enough CTAs for several waves over 152 SMs
-    int per = std::max(1, (nH12 * ktiles) / (152 * 8));
-    per = std::min(per, nH12);
-    size_t sm = (size_t)per * p.gm.nH[2] * p.nsite * sizeof(C);
-    while (sm > 96 * 1024 && per > 1) {
-        per = (per + 1) / 2;
-        sm = (size_t)per * p.gm.nH[2] * p.nsite * sizeof(C);
-    }
+    const size_t sm = (size_t)per * p.gm.nH[2] * p.nsite * sizeof(C);
     if (sm > 48 * 1024)
-        cudaFuncSetAttribute(k_recomb_cm<T, NC, MAXS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        cudaFuncSetAttribute(k_recomb_cm<T, NC, MAXS, ONECLS, VPI, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)sm);
     dim3 grid(ktiles, (nH12 + per - 1) / per);
-    k_recomb_cm<T, NC, MAXS><<<grid, 256, sm, s>>>(p, per);
+    k_recomb_cm<T, NC, MAXS, ONECLS, VPI, MINB><<<grid, 256, sm, s>>>(p, per);
     count_launches(1);
+}
+
+// Grouped variant: per (k, H1, H2) column the site sum is first reduced to one partial sum per
+// site group (sites of one form-factor class sharing z = r_mu,3 mod 1),
+//     A_g,c = sum_{mu in g} exp(2 pi i (H1 x_mu + H2 y_mu)) Y_mu,c(k),
+// and each voxel of the column then needs only
+//     F_c(H + k) = sum_g exp(2 pi i H3 z_g) A_g,c
+// (times the class form factor), i.e. n_groups instead of n_sites complex multiply-adds.
+template <typename T, int NC, int MAXS, int MAXG, bool ONECLS, int VPI, int MINB>
+__global__ void __launch_bounds__(256, MINB)
+    k_recomb_cm_grp(const __grid_constant__ RecombParams<T> p, int h12_per_cta) {
+    using C = c_t<T>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ int grp_end_s[MAX_SITES];
+    __shared__ int cls_grp_end_s[MAX_FF_CLASSES];
+    __shared__ int cls_kind_s[MAX_FF_CLASSES];
+    __shared__ T cls_coef_s[MAX_FF_CLASSES][9];
+    const Geometry &g = p.g;
+    const GridMap &gm = p.gm;
+    const int nsite = p.nsite, ngrp = p.grp.ngrp;
+    const int nH12 = gm.nH[0] * gm.nH[1];
+    const int h12_0 = blockIdx.y * h12_per_cta;
+    const int nh12 = min(h12_per_cta, nH12 - h12_0);
+    const int nH3 = gm.nH[2];
+    C *P12 = (C *)smem_raw;                           // [per][nsite]
+    C *W = P12 + (size_t)h12_per_cta * nsite;         // [nH3][ngrp]
+
+    if (threadIdx.x < MAX_SITES) grp_end_s[threadIdx.x] = p.grp.grp_end[threadIdx.x];
+    if (threadIdx.x < MAX_FF_CLASSES) {
+        cls_grp_end_s[threadIdx.x] = p.grp.cls_grp_end[threadIdx.x];
+        cls_kind_s[threadIdx.x] = p.ff.cls_kind[threadIdx.x];
+#pragma unroll
+        for (int j = 0; j < 9; ++j) cls_coef_s[threadIdx.x][j] = p.ff.cls_coef[threadIdx.x][j];
+    }
+    for (int idx = threadIdx.x; idx < nh12 * nsite; idx += blockDim.x) {
+        const int s = idx % nsite, j12 = idx / nsite;
+        const int h12 = h12_0 + j12;
+        const int h1 = h12 / gm.nH[1], h2 = h12 - h1 * gm.nH[1];
+        const C *t = p.phH + (size_t)p.site_of[s] * 3 * p.nHmax;
+        P12[idx] = cmul(t[h1], t[p.nHmax + h2]);
+    }
+    for (int idx = threadIdx.x; idx < nH3 * ngrp; idx += blockDim.x) {
+        const int gg = idx % ngrp, h3 = idx / ngrp;
+        W[idx] = p.phH[((size_t)p.grp.grp_site[gg] * 3 + 2) * p.nHmax + h3];
+    }
+    __syncthreads();
+
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= g.ncell) return;
+    const int k3 = k % g.n[2];
+    const int k2 = (k / g.n[2]) % g.n[1];
+    const int k1 = k / (g.n[2] * g.n[1]);
+    int h3lo = ceil_div(gm.g0[2] - k3, g.n[2]) - gm.Hmin[2];
+    int h3hi = floor_div(gm.g0[2] + gm.cnt[2] - 1 - k3, g.n[2]) - gm.Hmin[2];
+    h3lo = max(h3lo, 0);
+    h3hi = min(h3hi, nH3 - 1);
+
+    int conj;
+    const int kidx = half_index(g, k1, k2, k3, conj);
+    C Y[MAXS][NC];
+#pragma unroll
+    for (int s = 0; s < MAXS; ++s) {
+        if (s < nsite) {
+            const int site = p.site_of[s];
+            const C *t = p.phk + (size_t)site * 3 * p.nmax;
+            const C ph = cscale(cmul(cmul(t[k1], t[p.nmax + k2]), t[2 * p.nmax + k3]), p.scat[site]);
+#pragma unroll
+            for (int c = 0; c < NC; ++c) {
+                C x = p.spec[(((size_t)p.model * nsite + site) * NC + c) * g.ncell_h + kidx];
+                if (conj) x = cconj(x);
+                Y[s][c] = cmul(ph, x);
+            }
+        } else {
+#pragma unroll
+            for (int c = 0; c < NC; ++c) Y[s][c] = mk<T>(T(0), T(0));
+        }
+    }
+    const int kind0 = cls_kind_s[0];
+    const T inv16pi2 = (T)(1.0 / (FOUR_PI_D * FOUR_PI_D));
+
+    for (int j12 = 0; j12 < nh12; ++j12) {
+        const int h12 = h12_0 + j12;
+        const int h1 = h12 / gm.nH[1], h2 = h12 - h1 * gm.nH[1];
+        const int G1 = g.n[0] * (gm.Hmin[0] + h1) + k1;
+        const int G2 = g.n[1] * (gm.Hmin[1] + h2) + k2;
+        if (G1 < gm.g0[0] || G1 >= gm.g0[0] + gm.cnt[0]) continue;
+        if (G2 < gm.g0[1] || G2 >= gm.g0[1] + gm.cnt[1]) continue;
+        // group sums of this column
+        C A[MAXG][NC];
+#pragma unroll
+        for (int gg = 0; gg < MAXG; ++gg)
+#pragma unroll
+            for (int c = 0; c < NC; ++c) A[gg][c] = mk<T>(T(0), T(0));
+        {
+            const C *Pr = P12 + (size_t)j12 * nsite;
+            C part[NC];
+#pragma unroll
+            for (int c = 0; c < NC; ++c) part[c] = mk<T>(T(0), T(0));
+            int gcur = 0;
+#pragma unroll
+            for (int s = 0; s < MAXS; ++s) {
+                if (s < nsite) {
+                    const C ps = Pr[s];
+#pragma unroll
+                    for (int c = 0; c < NC; ++c) cfma(part[c], ps, Y[s][c]);
+                    if (s + 1 == grp_end_s[gcur]) {
+#pragma unroll
+                        for (int gg = 0; gg < MAXG; ++gg)
+                            if (gg == gcur)
+#pragma unroll
+                                for (int c = 0; c < NC; ++c) A[gg][c] = part[c];
+#pragma unroll
+                        for (int c = 0; c < NC; ++c) part[c] = mk<T>(T(0), T(0));
+                        ++gcur;
+                    }
+                }
+            }
+        }
+        T *orow = p.out + ((size_t)(G1 - gm.g0[0]) * gm.cnt[1] + (G2 - gm.g0[1])) * gm.cnt[2] - gm.g0[2];
+        T Q12[3], c3[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            Q12[a] = (T)((double)G1 / g.n[0] * p.recip[a] + (double)G2 / g.n[1] * p.recip[3 + a]);
+            c3[a] = (T)(p.recip[6 + a] / g.n[2]);
+        }
+        for (int h3 = h3lo; h3 <= h3hi; h3 += VPI) {
+            C F[VPI][NC], part[VPI][NC];
+            T s2[VPI], Qv[VPI][3], q2[VPI];
+#pragma unroll
+            for (int v = 0; v < VPI; ++v) {
+                const int G3 = g.n[2] * (gm.Hmin[2] + min(h3 + v, h3hi)) + k3;
+#pragma unroll
+                for (int a = 0; a < 3; ++a) Qv[v][a] = fma((T)G3, c3[a], Q12[a]);
+                q2[v] = Qv[v][0] * Qv[v][0] + Qv[v][1] * Qv[v][1] + Qv[v][2] * Qv[v][2];
+                s2[v] = q2[v] * inv16pi2;
+#pragma unroll
+                for (int c = 0; c < NC; ++c) F[v][c] = part[v][c] = mk<T>(T(0), T(0));
+            }
+            int cls = 0;
+#pragma unroll
+            for (int gg = 0; gg < MAXG; ++gg) {
+                if (gg < ngrp) {
+#pragma unroll
+                    for (int v = 0; v < VPI; ++v) {
+                        const C w = W[min(h3 + v, h3hi) * ngrp + gg];
+#pragma unroll
+                        for (int c = 0; c < NC; ++c) cfma(ONECLS ? F[v][c] : part[v][c], w, A[gg][c]);
+                    }
+                    if (!ONECLS && gg + 1 == cls_grp_end_s[cls]) {
+#pragma unroll
+                        for (int v = 0; v < VPI; ++v) {
+                            const T f = form_factor<T>(cls_kind_s[cls], cls_coef_s[cls], s2[v]);
+#pragma unroll
+                            for (int c = 0; c < NC; ++c) {
+                                F[v][c].x = fma(f, part[v][c].x, F[v][c].x);
+                                F[v][c].y = fma(f, part[v][c].y, F[v][c].y);
+                                part[v][c] = mk<T>(T(0), T(0));
+                            }
+                        }
+                        ++cls;
+                    }
+                }
+            }
+#pragma unroll
+            for (int v = 0; v < VPI; ++v) {
+                if (h3 + v > h3hi) break;
+                T tot = T(0);
+#pragma unroll
+                for (int c = 0; c < NC; ++c) tot += F[v][c].x * F[v][c].x + F[v][c].y * F[v][c].y;
+                T I = tot;
+                if (NC == 3) {
+                    if (q2[v] > T(0)) {
+                        const T pr = Qv[v][0] * F[v][0].x + Qv[v][1] * F[v][1].x + Qv[v][2] * F[v][2].x;
+                        const T pi = Qv[v][0] * F[v][0].y + Qv[v][1] * F[v][1].y + Qv[v][2] * F[v][2].y;
+                        I = tot - (pr * pr + pi * pi) / q2[v];
+                    } else {
+                        I = T(2) / T(3) * tot;
+                    }
+                }
+                if (ONECLS && kind0 != 0) {
+                    const T f = form_factor<T>(kind0, cls_coef_s[0], s2[v]);
+                    I *= f * f;
+                }
+                T *dst = orow + g.n[2] * (gm.Hmin[2] + h3 + v) + k3;
+                const T val = p.norm * I;
+                *dst = p.accumulate ? *dst + val : val;
+            }
+        }
+    }
+}
+
+template <typename T, int NC, int MAXS, int MAXG, bool ONECLS, int VPI, int MINB>
+void launch_cm_grp_variant(const RecombParams<T> &p, int per, cudaStream_t s) {
+    using C = c_t<T>;
+    const int nH12 = p.gm.nH[0] * p.gm.nH[1];
+    const int ktiles = (p.g.ncell + 255) / 256;
+    const size_t sm = ((size_t)per * p.nsite + (size_t)p.gm.nH[2] * p.grp.ngrp) * sizeof(C);
+    if (sm > 48 * 1024)
+        cudaFuncSetAttribute(k_recomb_cm_grp<T, NC, MAXS, MAXG, ONECLS, VPI, MINB>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    dim3 grid(ktiles, (nH12 + per - 1) / per);
+    k_recomb_cm_grp<T, NC, MAXS, MAXG, ONECLS, VPI, MINB><<<grid, 256, sm, s>>>(p, per);
+    count_launches(1);
+}
+
+// (H1, H2) columns per CTA: enough CTAs for several waves, shared table within budget
+template <typename T> static int cm_columns_per_cta(const RecombParams<T> &p, int waves_target) {
+    using C = c_t<T>;
+    const int nH12 = p.gm.nH[0] * p.gm.nH[1];
+    const int ktiles = (p.g.ncell + 255) / 256;
+    int per = std::max(1, (nH12 * ktiles) / (152 * waves_target));
+    per = std::min(per, nH12);
+    while ((size_t)per * p.gm.nH[2] * p.nsite * sizeof(C) > 96 * 1024 && per > 1) per = (per + 1) / 2;
+    return per;
+}
+
+template <typename T, int NC, int MAXS> static void launch_cm(const RecombParams<T> &p, cudaStream_t s) {
+    const int per = cm_columns_per_cta<T>(p, 8);
+    const bool one = p.ff.ncls == 1;
+    const int ng = p.grp.ngrp;
+    // grouping pays when the groups are at most half the sites
+    constexpr int GMINB = (NC == 3 && MAXS >= 16) ? 1 : 2;
+    if (2 * ng <= p.nsite && ng <= 8) {
+        if (ng <= 4) {
+            if (one) launch_cm_grp_variant<T, NC, MAXS, 4, true, 2, GMINB>(p, per, s);
+            else launch_cm_grp_variant<T, NC, MAXS, 4, false, 1, GMINB>(p, per, s);
+        } else {
+            if (one) launch_cm_grp_variant<T, NC, MAXS, 8, true, 2, GMINB>(p, per, s);
+            else launch_cm_grp_variant<T, NC, MAXS, 8, false, 1, GMINB>(p, per, s);
+        }
+        return;
+    }
+    if (one) launch_cm_variant<T, NC, MAXS, true, NC == 3 ? 2 : 1, 2>(p, per, s);
+    else launch_cm_variant<T, NC, MAXS, false, 1, 2>(p, per, s);
 }
 
 template <typename T> void recombine_cm(const RecombParams<T> &p, cudaStream_t s) {

@@ -188,3 +188,20 @@ def test_pyrochlore_occ_mag_20cubed(ctx):
         else:
             want_d = core.magnetic_intensity_direct(model, G[idx] / 20.0, mode)
         assert np.max(np.abs(I64f[idx] - want_d)) < 1e-10 * peak
+
+
+@pytest.mark.parametrize("dis", [0, 1])
+def test_grouped_sites_several_form_factor_classes(ctx, dis):
+    """Pyrochlore sites share z coordinates, so the recombination sums sites group by group;
+    two form-factor classes (constant and <j0>) and two supercells, FP64 and FP32."""
+    m = syn.pyrochlore_occ_mag(cells=(5, 4, 6), nmodels=2, hmax=1.0, seed=9)
+    m.ff_kind = np.array([0] * 8 + [2] * 8, dtype=np.int32)
+    m.ff_coef = np.zeros((16, 9))
+    m.ff_coef[8:, :7] = syn.J0_COEF
+    m.scat_len = np.linspace(0.5, 2.0, 16)
+    lm = to_library(ctx, m)
+    for prec, tag in PREC:
+        got, _ = lm.intensity(qgrid_tuple(m.qgrid), disorder=dis, mode=1, precision=prec)
+        fn = core.occupancy_intensity_fft if dis == 0 else core.magnetic_intensity_fft
+        want = fn(m, _G(m), 1)
+        assert rel_err_of_peak(got, want) < TOL[tag]
