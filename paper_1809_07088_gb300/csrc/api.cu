@@ -623,6 +623,7 @@ ds_status plan_and_run(ds_model *M, const ds_qgrid *q, const ds_opts *o, T *d_ou
     p.phk = phk;
     p.phH = phH;
     p.site_of = M->d_site_of;
+    p.sites = M->d_sites;
     if constexpr (sizeof(T) == 4) p.scat = M->d_scat32;
     else p.scat = M->d_scat64;
     p.out = d_out;

@@ -83,12 +83,23 @@ constexpr int MAX_FF_CLASSES = 8; // distinct non-constant form factors per requ
 constexpr double TWO_PI_D = 6.283185307179586476925286766559;
 constexpr double FOUR_PI_D = 12.566370614359172953850573533118;
 
+// exponential of the working precision: CUDA's exp in FP64, its fast __expf intrinsic in FP32
+// (a few ulp, far inside the FP32 path's error budget)
+__device__ __forceinline__ double exp_w(double x) { return exp(x); }
+__device__ __forceinline__ float exp_w(float x) { return __expf(x); }
+__device__ __forceinline__ double div_w(double a, double b) { return a / b; }
+__device__ __forceinline__ float div_w(float a, float b) { return __fdividef(a, b); }
+
 // form factor of one class at s^2 = (|Q|/4pi)^2; kind 0 = 1, 1 = 4-Gaussian, 2 = <j0>
 template <typename T> __device__ __forceinline__ T form_factor(int kind, const T *c, T s2) {
     if (kind == 1)
-        return c[0] * exp(-c[4] * s2) + c[1] * exp(-c[5] * s2) + c[2] * exp(-c[6] * s2) +
-               c[3] * exp(-c[7] * s2) + c[8];
-    if (kind == 2) return c[0] * exp(-c[1] * s2) + c[2] * exp(-c[3] * s2) + c[4] * exp(-c[5] * s2) + c[6];
+        return c[0] * exp_w(-c[4] * s2) + c[1] * exp_w(-c[5] * s2) + c[2] * exp_w(-c[6] * s2) +
+               c[3] * exp_w(-c[7] * s2) + c[8];
+    if (kind == 2) {
+        T f = c[6] + c[0] * exp_w(-c[1] * s2) + c[2] * exp_w(-c[3] * s2);
+        if (c[4] != T(0)) f += c[4] * exp_w(-c[5] * s2);
+        return f;
+    }
     return T(1);
 }
 

@@ -86,6 +86,7 @@ template <typename T> struct RecombParams {
     const c_t<T> *phH;                  // [site][3][nHmax]  exp(2 pi i H_a r_a)
     int nmax, nHmax;
     const int *site_of;                 // sorted position -> site
+    const double *sites;                // fractional site coordinates [site][3]
     const T *scat;                      // b per site
     FormFactors<T> ff;
     SiteGroups grp;

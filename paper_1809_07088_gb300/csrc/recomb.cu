@@ -325,7 +325,7 @@ __global__ void __launch_bounds__(256, MINB)
                     if (q2[v] > T(0)) {
                         const T pr = Qv[v][0] * F[v][0].x + Qv[v][1] * F[v][1].x + Qv[v][2] * F[v][2].x;
                         const T pi = Qv[v][0] * F[v][0].y + Qv[v][1] * F[v][1].y + Qv[v][2] * F[v][2].y;
-                        I = tot - (pr * pr + pi * pi) / q2[v];
+                        I = tot - div_w(pr * pr + pi * pi, q2[v]);
                     } else {
                         I = T(2) / T(3) * tot;
                     }
@@ -362,7 +362,7 @@ void launch_cm_variant(const RecombParams<T> &p, int per, cudaStream_t s) {
 // and each voxel of the column then needs only
 //     F_c(H + k) = sum_g exp(2 pi i H3 z_g) A_g,c
 // (times the class form factor), i.e. n_groups instead of n_sites complex multiply-adds.
-template <typename T, int NC, int MAXS, int MAXG, bool ONECLS, int VPI, int MINB>
+template <typename T, int NC, int MAXS, int MAXG, bool ONECLS, int VPI, int MINB, bool YSMEM>
 __global__ void __launch_bounds__(256, MINB)
     k_recomb_cm_grp(const __grid_constant__ RecombParams<T> p, int h12_per_cta) {
     using C = c_t<T>;
@@ -379,7 +379,8 @@ __global__ void __launch_bounds__(256, MINB)
     const int nh12 = min(h12_per_cta, nH12 - h12_0);
     const int nH3 = gm.nH[2];
     C *P12 = (C *)smem_raw;                           // [per][nsite]
-    C *W = P12 + (size_t)h12_per_cta * nsite;         // [nH3][ngrp]
+    C *W = P12 + (size_t)h12_per_cta * nsite;         // [nH3 + 1][ngrp]
+    C *Ys = W + (size_t)(nH3 + 1) * ngrp;             // YSMEM: [nsite][NC][256]
 
     if (threadIdx.x < MAX_SITES) grp_end_s[threadIdx.x] = p.grp.grp_end[threadIdx.x];
     if (threadIdx.x < MAX_FF_CLASSES) {
@@ -395,9 +396,18 @@ __global__ void __launch_bounds__(256, MINB)
         const C *t = p.phH + (size_t)p.site_of[s] * 3 * p.nHmax;
         P12[idx] = cmul(t[h1], t[p.nHmax + h2]);
     }
-    for (int idx = threadIdx.x; idx < nH3 * ngrp; idx += blockDim.x) {
+    for (int idx = threadIdx.x; idx < (nH3 + 1) * ngrp; idx += blockDim.x) {
         const int gg = idx % ngrp, h3 = idx / ngrp;
-        W[idx] = p.phH[((size_t)p.grp.grp_site[gg] * 3 + 2) * p.nHmax + h3];
+        if (h3 < nH3) {
+            W[idx] = p.phH[((size_t)p.grp.grp_site[gg] * 3 + 2) * p.nHmax + h3];
+        } else {
+            // exp(2 pi i z_g), z_g = r_3 mod 1 of the group's site
+            double z = p.sites[3 * p.grp.grp_site[gg] + 2];
+            z -= floor(z);
+            double sn, cs;
+            sincospi(2.0 * z, &sn, &cs);
+            W[idx] = mk<T>((T)cs, (T)sn);
+        }
     }
     __syncthreads();
 
@@ -413,7 +423,7 @@ __global__ void __launch_bounds__(256, MINB)
 
     int conj;
     const int kidx = half_index(g, k1, k2, k3, conj);
-    C Y[MAXS][NC];
+    C Y[YSMEM ? 1 : MAXS][NC];
 #pragma unroll
     for (int s = 0; s < MAXS; ++s) {
         if (s < nsite) {
@@ -424,11 +434,12 @@ __global__ void __launch_bounds__(256, MINB)
             for (int c = 0; c < NC; ++c) {
                 C x = p.spec[(((size_t)p.model * nsite + site) * NC + c) * g.ncell_h + kidx];
                 if (conj) x = cconj(x);
-                Y[s][c] = cmul(ph, x);
+                if (YSMEM) Ys[((size_t)s * NC + c) * 256 + threadIdx.x] = cmul(ph, x);
+                else Y[YSMEM ? 0 : s][c] = cmul(ph, x);
             }
-        } else {
+        } else if (!YSMEM) {
 #pragma unroll
-            for (int c = 0; c < NC; ++c) Y[s][c] = mk<T>(T(0), T(0));
+            for (int c = 0; c < NC; ++c) Y[YSMEM ? 0 : s][c] = mk<T>(T(0), T(0));
         }
     }
     const int kind0 = cls_kind_s[0];
@@ -458,7 +469,10 @@ __global__ void __launch_bounds__(256, MINB)
                 if (s < nsite) {
                     const C ps = Pr[s];
 #pragma unroll
-                    for (int c = 0; c < NC; ++c) cfma(part[c], ps, Y[s][c]);
+                    for (int c = 0; c < NC; ++c) {
+                        const C y = YSMEM ? Ys[((size_t)s * NC + c) * 256 + threadIdx.x] : Y[YSMEM ? 0 : s][c];
+                        cfma(part[c], ps, y);
+                    }
                     if (s + 1 == grp_end_s[gcur]) {
 #pragma unroll
                         for (int gg = 0; gg < MAXG; ++gg)
@@ -479,12 +493,21 @@ __global__ void __launch_bounds__(256, MINB)
             Q12[a] = (T)((double)G1 / g.n[0] * p.recip[a] + (double)G2 / g.n[1] * p.recip[3 + a]);
             c3[a] = (T)(p.recip[6 + a] / g.n[2]);
         }
+        // exp(2 pi i H3 z_g) of the first voxel, then advanced by exp(2 pi i z_g) per zone step
+        C wcur[MAXG], wstep[MAXG];
+#pragma unroll
+        for (int gg = 0; gg < MAXG; ++gg) {
+            if (gg < ngrp) {
+                wcur[gg] = W[h3lo * ngrp + gg];
+                wstep[gg] = W[nH3 * ngrp + gg];
+            }
+        }
         for (int h3 = h3lo; h3 <= h3hi; h3 += VPI) {
             C F[VPI][NC], part[VPI][NC];
             T s2[VPI], Qv[VPI][3], q2[VPI];
 #pragma unroll
             for (int v = 0; v < VPI; ++v) {
-                const int G3 = g.n[2] * (gm.Hmin[2] + min(h3 + v, h3hi)) + k3;
+                const int G3 = g.n[2] * (gm.Hmin[2] + h3 + v) + k3;
 #pragma unroll
                 for (int a = 0; a < 3; ++a) Qv[v][a] = fma((T)G3, c3[a], Q12[a]);
                 q2[v] = Qv[v][0] * Qv[v][0] + Qv[v][1] * Qv[v][1] + Qv[v][2] * Qv[v][2];
@@ -498,9 +521,10 @@ __global__ void __launch_bounds__(256, MINB)
                 if (gg < ngrp) {
 #pragma unroll
                     for (int v = 0; v < VPI; ++v) {
-                        const C w = W[min(h3 + v, h3hi) * ngrp + gg];
+                        const C w = wcur[gg];
 #pragma unroll
                         for (int c = 0; c < NC; ++c) cfma(ONECLS ? F[v][c] : part[v][c], w, A[gg][c]);
+                        wcur[gg] = cmul(wcur[gg], wstep[gg]);
                     }
                     if (!ONECLS && gg + 1 == cls_grp_end_s[cls]) {
 #pragma unroll
@@ -517,45 +541,47 @@ __global__ void __launch_bounds__(256, MINB)
                     }
                 }
             }
+            T val[VPI];
 #pragma unroll
             for (int v = 0; v < VPI; ++v) {
-                if (h3 + v > h3hi) break;
                 T tot = T(0);
 #pragma unroll
                 for (int c = 0; c < NC; ++c) tot += F[v][c].x * F[v][c].x + F[v][c].y * F[v][c].y;
                 T I = tot;
                 if (NC == 3) {
-                    if (q2[v] > T(0)) {
-                        const T pr = Qv[v][0] * F[v][0].x + Qv[v][1] * F[v][1].x + Qv[v][2] * F[v][2].x;
-                        const T pi = Qv[v][0] * F[v][0].y + Qv[v][1] * F[v][1].y + Qv[v][2] * F[v][2].y;
-                        I = tot - (pr * pr + pi * pi) / q2[v];
-                    } else {
-                        I = T(2) / T(3) * tot;
-                    }
+                    const T pr = Qv[v][0] * F[v][0].x + Qv[v][1] * F[v][1].x + Qv[v][2] * F[v][2].x;
+                    const T pi = Qv[v][0] * F[v][0].y + Qv[v][1] * F[v][1].y + Qv[v][2] * F[v][2].y;
+                    I = q2[v] > T(0) ? tot - div_w(pr * pr + pi * pi, q2[v]) : T(2) / T(3) * tot;
                 }
                 if (ONECLS && kind0 != 0) {
                     const T f = form_factor<T>(kind0, cls_coef_s[0], s2[v]);
                     I *= f * f;
                 }
-                T *dst = orow + g.n[2] * (gm.Hmin[2] + h3 + v) + k3;
-                const T val = p.norm * I;
-                *dst = p.accumulate ? *dst + val : val;
+                val[v] = p.norm * I;
+            }
+#pragma unroll
+            for (int v = 0; v < VPI; ++v) {
+                if (h3 + v <= h3hi) {
+                    T *dst = orow + g.n[2] * (gm.Hmin[2] + h3 + v) + k3;
+                    *dst = p.accumulate ? *dst + val[v] : val[v];
+                }
             }
         }
     }
 }
 
-template <typename T, int NC, int MAXS, int MAXG, bool ONECLS, int VPI, int MINB>
+template <typename T, int NC, int MAXS, int MAXG, bool ONECLS, int VPI, int MINB, bool YSMEM = false>
 void launch_cm_grp_variant(const RecombParams<T> &p, int per, cudaStream_t s) {
     using C = c_t<T>;
     const int nH12 = p.gm.nH[0] * p.gm.nH[1];
     const int ktiles = (p.g.ncell + 255) / 256;
-    const size_t sm = ((size_t)per * p.nsite + (size_t)p.gm.nH[2] * p.grp.ngrp) * sizeof(C);
+    size_t sm = ((size_t)per * p.nsite + (size_t)(p.gm.nH[2] + 1) * p.grp.ngrp) * sizeof(C);
+    if (YSMEM) sm += (size_t)p.nsite * NC * 256 * sizeof(C);
     if (sm > 48 * 1024)
-        cudaFuncSetAttribute(k_recomb_cm_grp<T, NC, MAXS, MAXG, ONECLS, VPI, MINB>,
+        cudaFuncSetAttribute(k_recomb_cm_grp<T, NC, MAXS, MAXG, ONECLS, VPI, MINB, YSMEM>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     dim3 grid(ktiles, (nH12 + per - 1) / per);
-    k_recomb_cm_grp<T, NC, MAXS, MAXG, ONECLS, VPI, MINB><<<grid, 256, sm, s>>>(p, per);
+    k_recomb_cm_grp<T, NC, MAXS, MAXG, ONECLS, VPI, MINB, YSMEM><<<grid, 256, sm, s>>>(p, per);
     count_launches(1);
 }
 
@@ -575,14 +601,26 @@ template <typename T, int NC, int MAXS> static void launch_cm(const RecombParams
     const bool one = p.ff.ncls == 1;
     const int ng = p.grp.ngrp;
     // grouping pays when the groups are at most half the sites
-    constexpr int GMINB = (NC == 3 && MAXS >= 16) ? 1 : 2;
+    // measured on GB300 (16 sites, 20^3 cells, 241^3 voxels): magnetic fastest with 2 CTAs/SM
+    // and Y in registers; occupancy with Y staged in shared memory and 4 CTAs/SM
     if (2 * ng <= p.nsite && ng <= 8) {
-        if (ng <= 4) {
-            if (one) launch_cm_grp_variant<T, NC, MAXS, 4, true, 2, GMINB>(p, per, s);
-            else launch_cm_grp_variant<T, NC, MAXS, 4, false, 1, GMINB>(p, per, s);
+        const int per4 = cm_columns_per_cta<T>(p, 4);
+        if (NC == 3) {
+            if (ng <= 4) {
+                if (one) launch_cm_grp_variant<T, NC, MAXS, 4, true, 1, 2>(p, per4, s);
+                else launch_cm_grp_variant<T, NC, MAXS, 4, false, 1, 2>(p, per4, s);
+            } else {
+                if (one) launch_cm_grp_variant<T, NC, MAXS, 8, true, 1, 2>(p, per4, s);
+                else launch_cm_grp_variant<T, NC, MAXS, 8, false, 1, 2>(p, per4, s);
+            }
         } else {
-            if (one) launch_cm_grp_variant<T, NC, MAXS, 8, true, 2, GMINB>(p, per, s);
-            else launch_cm_grp_variant<T, NC, MAXS, 8, false, 1, GMINB>(p, per, s);
+            if (ng <= 4) {
+                if (one) launch_cm_grp_variant<T, NC, MAXS, 4, true, 1, 4, true>(p, per4, s);
+                else launch_cm_grp_variant<T, NC, MAXS, 4, false, 1, 4, true>(p, per4, s);
+            } else {
+                if (one) launch_cm_grp_variant<T, NC, MAXS, 8, true, 1, 4, true>(p, per4, s);
+                else launch_cm_grp_variant<T, NC, MAXS, 8, false, 1, 4, true>(p, per4, s);
+            }
         }
         return;
     }
