@@ -168,6 +168,28 @@ ds_status ds_backward(ds_model *model, const ds_qgrid *grid, const ds_opts *opts
 ds_status ds_profile_enable(ds_ctx *ctx, int enable);
 ds_status ds_profile_report(ds_ctx *ctx, char *json, size_t cap);
 
+/* Occupancy intensity for callers that cannot allocate device memory (no counterpart in the
+ * paper): a host application or framework that owns all GPU memory through its own allocator,
+ * a process running under a fixed memory cap, or a refinement loop that must not call the
+ * allocator between iterations.  Same result as ds_request_intensity with DS_OCC, DS_FP32 and
+ * constant form factors (f = 1, amplitude scat_len), computed on the CURRENT device without any
+ * allocation: every intermediate lives in one static device array of 32 MiB that each GPU
+ * loading the library holds until exit.
+ *   lattice[6]      a, b, c (A), alpha, beta, gamma (deg);  nsite <= 32 sites at frac_xyz[nsite*3]
+ *   scat_len        [nsite] host, NULL = 1;  n1 n2 n3, nmodels as for ds_model_set_supercell
+ *   occ_dev         device uint8 [model][site][n1][n2][n3];  mean_occ [nsite] host or NULL
+ *   grid, mode      as for ds_request_intensity (commensurate grid; DS_TOTAL / DS_DIFFUSE)
+ *   out_dev         device float [count0][count1][count2], written in stream order on `stream`
+ *   err, errlen     optional buffer for a message on failure
+ * Requests whose scratch exceeds 32 MiB return DS_ERR_ADMISSION (message gives the size).
+ * The first call on a device looks up the array's address with that device current: make it
+ * before any stream capture.  All calls share the array; calls whose GPU work overlaps race on
+ * it and must be serialised by the caller.  Nothing in the array needs clearing between calls. */
+ds_status ds_occupancy_intensity_noalloc(const double lattice[6], int nsite, const double *frac_xyz,
+                                         const double *scat_len, int n1, int n2, int n3, int nmodels,
+                                         const uint8_t *occ_dev, const double *mean_occ, const ds_qgrid *grid,
+                                         int mode, float *out_dev, void *stream, char *err, size_t errlen);
+
 #ifdef __cplusplus
 }
 #endif

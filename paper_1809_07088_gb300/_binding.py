@@ -67,6 +67,9 @@ SIGNATURES = {
     "ds_backward": (st, [vp, C.POINTER(ds_qgrid), C.POINTER(ds_opts), vp, vp, C.c_int, vp]),
     "ds_profile_enable": (st, [vp, C.c_int]),
     "ds_profile_report": (st, [vp, C.c_char_p, C.c_size_t]),
+    "ds_occupancy_intensity_noalloc": (st, [C.POINTER(C.c_double), C.c_int, vp, vp, C.c_int, C.c_int, C.c_int,
+                                            C.c_int, vp, vp, C.POINTER(ds_qgrid), C.c_int, vp, vp, C.c_char_p,
+                                            C.c_size_t]),
 }
 
 _lib = None

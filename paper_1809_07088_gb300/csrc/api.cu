@@ -49,7 +49,7 @@ ds_status ds_fail(ds_ctx *ctx, ds_status st, const char *fmt, ...) {
 // geometry helpers (host, FP64)
 // ------------------------------------------------------------------------------------------
 
-static void lattice_matrices(const double lat[6], double A[9], double B[9]) {
+void lattice_matrices(const double lat[6], double A[9], double B[9]) {
     const double d2r = 3.14159265358979323846 / 180.0;
     const double a = lat[0], b = lat[1], c = lat[2];
     const double al = lat[3] * d2r, be = lat[4] * d2r, ga = lat[5] * d2r;

@@ -113,6 +113,7 @@ template <typename T> struct ForwardKeep {
     const T *pw = nullptr;
 };
 
+void lattice_matrices(const double lat[6], double A[9], double B[9]);
 bool make_geometry(const int n[3], ds::Geometry &g);
 ds::GridMap grid_map(const ds::Geometry &g, const int g0[3], const int cnt[3]);
 ds_status grid_indices(ds_ctx *ctx, const ds_model *M, const ds_qgrid *q, int g0[3], int cnt[3]);
