@@ -715,6 +715,10 @@ ds_status plan_and_run(ds_model *M, const ds_qgrid *q, const ds_opts *o, T *d_ou
     p.spec = spec;
 
     // recombination over the requested voxels (+ Bragg term)
+    if (keep && keep->Fout) {
+        p.Fout = keep->Fout;
+        p.force_plain = 1;
+    }
     if (o->disorder == DS_DISP) {
         if (p.diffuse) {
             C *avg0 = (C *)ws.get(sizeof(C) * nsite * Tn);

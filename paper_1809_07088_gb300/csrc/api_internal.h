@@ -111,6 +111,7 @@ template <typename T> struct ForwardKeep {
     const ds::c_t<T> *W[3];
     const int4 *terms = nullptr;
     const T *pw = nullptr;
+    ds::c_t<T> *Fout = nullptr;   // requested: F per voxel is written here
 };
 
 void lattice_matrices(const double lat[6], double A[9], double B[9]);

@@ -97,6 +97,8 @@ template <typename T> struct RecombParams {
     const int4 *terms;                  // displacive monomials (a, b, c, n)
     const c_t<T> *bragg;                // displacive DIFFUSE: <F(H)> per zone [nH1][nH2][nH3]
     T *out;                             // [cnt1][cnt2][cnt3]
+    c_t<T> *Fout;                       // optional: F per voxel [model][voxel][ncomp] (adjoint)
+    int force_plain;                    // use the per-site (ungrouped) recombination
     int *err;
 };
 

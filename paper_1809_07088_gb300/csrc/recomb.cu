@@ -330,13 +330,21 @@ __global__ void __launch_bounds__(256, MINB)
                         I = T(2) / T(3) * tot;
                     }
                 }
+                T fone = T(1);
                 if (ONECLS && kind0 != 0) {
-                    const T f = form_factor<T>(kind0, cls_coef_s[0], s2[v]);
-                    I *= f * f;
+                    fone = form_factor<T>(kind0, cls_coef_s[0], s2[v]);
+                    I *= fone * fone;
                 }
                 T *dst = orow + g.n[2] * (gm.Hmin[2] + h3 + v) + k3;
                 const T val = p.norm * I;
                 *dst = p.accumulate ? *dst + val : val;
+                if (p.Fout) {
+                    const size_t vi = (size_t)(dst - p.out);
+                    const size_t nv = (size_t)gm.cnt[0] * gm.cnt[1] * gm.cnt[2];
+#pragma unroll
+                    for (int c = 0; c < NC; ++c)
+                        p.Fout[((size_t)p.model * nv + vi) * NC + c] = cscale(F[v][c], fone);
+                }
             }
         }
     }
@@ -599,7 +607,7 @@ template <typename T> static int cm_columns_per_cta(const RecombParams<T> &p, in
 template <typename T, int NC, int MAXS> static void launch_cm(const RecombParams<T> &p, cudaStream_t s) {
     const int per = cm_columns_per_cta<T>(p, 8);
     const bool one = p.ff.ncls == 1;
-    const int ng = p.grp.ngrp;
+    const int ng = p.force_plain ? p.nsite : p.grp.ngrp;
     // grouping pays when the groups are at most half the sites
     // measured on GB300 (16 sites, 20^3 cells, 241^3 voxels): magnetic fastest with 2 CTAs/SM
     // and Y in registers; occupancy with Y staged in shared memory and 4 CTAs/SM
@@ -813,6 +821,7 @@ __global__ void __launch_bounds__(DISP_KT * 32) k_recomb_disp(RecombParams<T> p)
         const size_t v = ((size_t)(G1 - gm.g0[0]) * gm.cnt[1] + (G2 - gm.g0[1])) * gm.cnt[2] + (G3 - gm.g0[2]);
         const T val = p.norm * I;
         p.out[v] = p.accumulate ? p.out[v] + val : val;
+        if (p.Fout) p.Fout[(size_t)p.model * gm.cnt[0] * gm.cnt[1] * gm.cnt[2] + v] = F;
     }
 }
 

@@ -205,3 +205,87 @@ def test_grouped_sites_several_form_factor_classes(ctx, dis):
         fn = core.occupancy_intensity_fft if dis == 0 else core.magnetic_intensity_fft
         want = fn(m, _G(m), 1)
         assert rel_err_of_peak(got, want) < TOL[tag]
+
+
+@pytest.mark.parametrize("disorder,kind", [("occ", 0), ("spin", 1)])
+@pytest.mark.parametrize("nsb,mode", [(1, 1), (2, 0), (3, 1)])
+def test_subbox_against_brute_force(ctx, disorder, kind, nsb, mode):
+    """Section V A: every lattice point the origin of an n_sb^3 open box; the GPU pair-spectrum
+    route against the oracle's literal loop over origins (commensurate grid)."""
+    m = syn.small_case(syn.OCC if kind == 0 else syn.SPIN, cells=(6, 7, 6), nsite=3, nmodels=2, seed=110 + nsb)
+    q = syn.QGrid(tuple(-1.0 - 1.0 / n for n in m.cells), tuple(1.0 / n for n in m.cells),
+                  tuple(n + 3 for n in m.cells))
+    lm = to_library(ctx, m)
+    # exact hkl = G / n (the float grid h0 + i * step misses Q = 0 by rounding)
+    want = noise.subbox_intensity(m, disorder, mode, nsb, q.g_index(m.cells) / np.array(m.cells, dtype=float))
+    for prec, tag in PREC:
+        got, _ = lm.intensity(qgrid_tuple(q), disorder=kind, mode=mode, precision=prec, smoothing=2, subbox_n=nsb)
+        assert rel_err_of_peak(got, want) < TOL[tag]
+
+
+# ----------------------------------------------------------------------------------------------
+# adjoint
+# ----------------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("prec,tol", [(0, 1e-9), (1, 2e-4)])
+def test_displacive_gradient_against_oracle(ctx, prec, tol):
+    """dchi^2/du through ds_backward (Taylor order high enough that truncation is below
+    rounding) against the oracle's chain rule of the exact direct sum, TOTAL mode."""
+    from oracle import adjoint
+    m = syn.small_case(syn.DISP, cells=(3, 4, 3), nsite=2, nmodels=2, seed=121, sigma=0.05)
+    t = syn.small_case(syn.DISP, cells=(3, 4, 3), nsite=2, nmodels=2, seed=122, sigma=0.04)
+    hkl = m.qgrid.g_index(m.cells) / np.array(m.cells, dtype=float)
+    target = core.displacive_intensity_direct(t, hkl, core.TOTAL)
+    chi2, g_or = adjoint.displacive_chi2_grad(m, hkl, target)
+    I = core.displacive_intensity_direct(m, hkl, core.TOTAL)
+    dLdI = (2.0 * (I - target)).reshape(m.qgrid.count)
+    lm = to_library(ctx, m)
+    dt = np.float64 if prec == 0 else np.float32
+    g = lm.backward(qgrid_tuple(m.qgrid), np.ascontiguousarray(dLdI, dtype=dt), disorder=2, mode=0,
+                    precision=prec, taylor_order=16)
+    assert g.shape == g_or.shape
+    assert np.max(np.abs(g - g_or)) < tol * np.max(np.abs(g_or))
+
+
+@pytest.mark.parametrize("prec,tol", [(0, 1e-10), (1, 1e-5)])
+def test_magnetic_gradient_against_oracle(ctx, prec, tol):
+    from oracle import adjoint
+    m = syn.small_case(syn.SPIN, cells=(4, 3, 5), nsite=3, nmodels=1, seed=123)
+    t = syn.small_case(syn.SPIN, cells=(4, 3, 5), nsite=3, nmodels=1, seed=124)
+    hkl = m.qgrid.g_index(m.cells) / np.array(m.cells, dtype=float)
+    target = core.magnetic_intensity_direct(t, hkl, core.TOTAL)
+    chi2, g_or = adjoint.magnetic_chi2_grad(m, hkl, target)
+    I = core.magnetic_intensity_direct(m, hkl, core.TOTAL)
+    dLdI = (2.0 * (I - target)).reshape(m.qgrid.count)
+    lm = to_library(ctx, m)
+    dt = np.float64 if prec == 0 else np.float32
+    g = lm.backward(qgrid_tuple(m.qgrid), np.ascontiguousarray(dLdI, dtype=dt), disorder=1, mode=0,
+                    precision=prec)
+    assert np.max(np.abs(g - g_or)) < tol * np.max(np.abs(g_or))
+
+
+def test_autograd_function_directional_derivative(ctx):
+    """torch.autograd through the library: <grad, v> equals the central difference of the
+    FP64 forward along v (dot-product test of the adjoint)."""
+    import torch
+    from paper_1809_07088_gb300.autograd import diffuse_intensity
+    m = syn.small_case(syn.DISP, cells=(4, 4, 4), nsite=2, nmodels=1, seed=125, sigma=0.05)
+    lm = to_library(ctx, m)
+    q = qgrid_tuple(m.qgrid)
+    u = torch.tensor(m.disp, dtype=torch.float32, device="cuda", requires_grad=True)
+    I = diffuse_intensity(lm, u, q, taylor_order=14, precision=0)
+    w = torch.linspace(-1.0, 1.0, I.numel(), device="cuda", dtype=I.dtype).reshape(I.shape)
+    L = (I * w).sum()
+    L.backward()
+    gu = u.grad.double().cpu().numpy()
+    rng = np.random.default_rng(0)
+    v = rng.standard_normal(m.disp.shape)
+    h = 1e-3
+    vals = []
+    for sgn in (1, -1):
+        up = torch.tensor(m.disp.astype(np.float64) + sgn * h * v, dtype=torch.float32, device="cuda")
+        Ip = diffuse_intensity(lm, up, q, taylor_order=14, precision=0)
+        vals.append(float((Ip * w).sum()))
+    fd = (vals[0] - vals[1]) / (2 * h)
+    ad = float(np.sum(gu * v))
+    assert abs(fd - ad) < 2e-3 * max(1.0, abs(ad))
