@@ -81,7 +81,7 @@ def barrier(device=None):
 
 
 class ClockSampler:
-    """nvidia-smi clocks / throttle reasons sampled every 100 ms while running."""
+    """nvidia-smi clocks / throttle reasons sampled every 20 ms while running."""
     FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -94,7 +94,7 @@ class ClockSampler:
     def start(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
-                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                          "--format=csv,noheader,nounits", "-lms", "20"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -346,28 +346,158 @@ def run_ours(args):
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline()
+    serving = None
+    lm_n.close()
+    lm_m.close()
+    ctx.close()
+    if args.serving > 0:
+        serving = run_serving(args.serving, nreq_fp64=min(32, args.serving))
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": workload_config({"parallelism": "replicas" if ws > 1 else "single GPU"}),
             "max_rel_err_vs_fp64": max(errs), "fp64_plain": {"ms_per_step": ms64, "value": ws * vox_step / (ms64 / 1e3)},
             "e2e": e2e, "roofline": roofline, "stages": stages, "gpu_launches": int(prof.get("launches", 0)),
-            "wall_ms_per_step": 1e3 * t_wall / args.steps, "clocks": clk, "cpu_baseline": cpu}
+            "wall_ms_per_step": 1e3 * t_wall / args.steps, "clocks": clk, "cpu_baseline": cpu,
+            "serving": serving}
     if rank == 0:
         print(json.dumps(line))
-    lm_n.close()
-    lm_m.close()
-    ctx.close()
     return 0
+
+
+# ----------------------------------------------------------------------------------------------
+# serving: Poisson arrivals of mixed requests through ds_submit / ds_wait
+# ----------------------------------------------------------------------------------------------
+
+SERVE_SIZES = (16, 32, 48, 64)
+SERVE_NSITE = (1, 2, 4, 8, 16)
+
+
+def _serving_pool(ds, ctx, syn):
+    """Resident models: supercells 16^3..64^3 x {occupancy, spin, displacement} x nsite buckets."""
+    import numpy as np
+    pool = {}
+    for n in SERVE_SIZES:
+        for kind in (0, 1, 2):
+            for ns in SERVE_NSITE:
+                spec = dict(n=n, kind=kind, nsite=ns, seed=1000 * n + 100 * kind + ns, hmax=4.0)
+                m = syn.serving_model(spec)
+                lm = ds.Model(ctx, m.lattice, m.sites, m.cells, 1, m.scat_len, m.ff_kind, m.ff_coef)
+                if m.occ is not None:
+                    lm.upload_occupancy(np.ascontiguousarray(m.occ))
+                if m.spins is not None:
+                    lm.upload_spins(np.ascontiguousarray(m.spins))
+                if m.disp is not None:
+                    lm.upload_displacements(np.ascontiguousarray(m.disp))
+                pool[(n, kind, ns)] = (lm, m)
+    return pool
+
+
+def _bucket(nsite):
+    return min(SERVE_NSITE, key=lambda b: (abs(b - nsite), b))
+
+
+def _serve_stream(ds, ctx, pool, reqs, precision, rate_hz, seed):
+    """Replay `reqs` with Poisson arrivals at rate_hz; returns per-request latency / gpu ms."""
+    import numpy as np
+    import threading
+    import torch
+    rng = np.random.default_rng(seed)
+    arrivals = np.cumsum(rng.exponential(1.0 / rate_hz, len(reqs)))
+    dt = torch.float64 if precision == 0 else torch.float32
+    pending = []
+    lock = threading.Lock()
+    cond = threading.Condition(lock)
+    done = {"n": 0}
+    results = []
+
+    def submitter():
+        t0 = time.perf_counter()
+        for t_arr, r in zip(arrivals, reqs):
+            lm, m = pool[(r["n"], r["kind"], _bucket(r["nsite"]))]
+            delay = t0 + t_arr - time.perf_counter()
+            if delay > 0:
+                time.sleep(delay)
+            out = torch.empty(m.qgrid.count, dtype=dt, device="cuda")
+            opts = dict(disorder=r["kind"], mode=1 if r["kind"] != 1 else 0, precision=precision)
+            if r["kind"] == 2:
+                opts.update(taylor_order=-1, taylor_eps=1e-6)
+            tk = lm.submit((m.qgrid.h0, m.qgrid.step, m.qgrid.count), out, **opts)
+            with cond:
+                pending.append((tk, out, m.qgrid.nvox))
+                cond.notify()
+
+    th = threading.Thread(target=submitter)
+    t_start = time.perf_counter()
+    th.start()
+    got = 0
+    while got < len(reqs):
+        with cond:
+            while not pending:
+                cond.wait(1.0)
+            tk, out, nvox = pending.pop(0)
+        info = ctx.wait(tk, 600.0)
+        results.append((info.latency_ms, info.gpu_ms, nvox))
+        del out
+        got += 1
+    th.join()
+    makespan = time.perf_counter() - t_start
+    lat = np.array([r[0] for r in results])
+    vox = sum(r[2] for r in results)
+    return {"requests": len(reqs), "rate_hz": rate_hz, "p50_ms": float(np.percentile(lat, 50)),
+            "p99_ms": float(np.percentile(lat, 99)), "mean_ms": float(lat.mean()),
+            "throughput": vox / makespan, "unit": UNIT, "makespan_s": makespan}
+
+
+def run_serving(nreq, nreq_fp64=32, seed=4):
+    """Mixed-request serving: calibrate the service time of each pool entry, then replay a
+    Poisson stream at ~70% utilisation (FP32), and a shorter one on the plain FP64 path."""
+    import numpy as np
+    import torch
+    import paper_1809_07088_gb300 as ds
+    import synthetic as syn
+    torch.cuda.set_device(0)
+    ctx = ds.Context(0, hbm_budget=64 << 30)
+    pool = _serving_pool(ds, ctx, syn)
+    reqs = syn.serving_mix(nreq=nreq, seed=seed)
+    out = {}
+    for precision, n in ((1, nreq), (0, nreq_fp64)):
+        # service time of each request type alone (warm, sequential)
+        svc = {}
+        sub = reqs[:n]
+        used = {(r["n"], r["kind"], _bucket(r["nsite"])) for r in sub}
+        for key, (lm, m) in pool.items():
+            if key not in used:
+                continue
+            o = torch.empty(m.qgrid.count, dtype=torch.float64 if precision == 0 else torch.float32, device="cuda")
+            opts = dict(disorder=key[1], mode=1 if key[1] != 1 else 0, precision=precision)
+            if key[1] == 2:
+                opts.update(taylor_order=-1, taylor_eps=1e-6)
+            lm.intensity((m.qgrid.h0, m.qgrid.step, m.qgrid.count), out=o, **opts)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            lm.intensity((m.qgrid.h0, m.qgrid.step, m.qgrid.count), out=o, **opts)
+            torch.cuda.synchronize()
+            svc[key] = time.perf_counter() - t0
+            del o
+        mean_svc = float(np.mean([svc[(r["n"], r["kind"], _bucket(r["nsite"]))] for r in sub]))
+        rate = 0.7 / mean_svc
+        out["fp32" if precision == 1 else "fp64_plain"] = _serve_stream(ds, ctx, pool, sub, precision, rate, seed)
+        out["fp32" if precision == 1 else "fp64_plain"]["mean_service_ms"] = 1e3 * mean_svc
+    for lm, _ in pool.values():
+        lm.close()
+    ctx.close()
+    return out
 
 
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serving", type=int, default=128, help="requests in the serving stream (0 = skip)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

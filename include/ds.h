@@ -97,6 +97,7 @@ typedef struct {
     int64_t nvox;            /* voxels written */
     int64_t workspace_bytes; /* device scratch used by the request */
     double gpu_ms;           /* device time of the request (0 when not measured) */
+    double latency_ms;       /* served requests: submit to completion (host clock), else 0 */
 } ds_result_info;
 
 typedef struct ds_ctx ds_ctx;     /* one GPU: streams, HBM budget, request queue */
@@ -144,13 +145,23 @@ ds_status ds_model_upload_displacements(ds_model *model, const float *disp, int 
 ds_status ds_request_intensity(ds_model *model, const ds_qgrid *grid, const ds_opts *opts, void *out,
                                int out_is_device, void *stream, ds_result_info *info);
 
-/* Serving: queue a request (device `out`, kept valid until completion); requests run
- * concurrently on the context's streams as the HBM budget allows (continuous batching). */
+/* Serving: queue a request (device `out`, kept valid until completion).  The call validates
+ * the request, chooses the Taylor order (displacive, reading x_max back on the context's own
+ * stream) and estimates its HBM footprint; a worker thread admits queued requests in arrival
+ * order while the footprints in flight fit the context's budget and runs each on one of eight
+ * streams, so the work of concurrent requests overlaps on the GPU.  Results do not depend on
+ * the mix.  The model must not be modified while its requests are in flight.  Errors:
+ * DS_ERR_ADMISSION (larger than the whole budget), the errors of ds_request_intensity. */
 ds_status ds_submit(ds_model *model, const ds_qgrid *grid, const ds_opts *opts, void *out, uint64_t *ticket);
 /* DS_OK when finished (info filled), DS_ERR_STATE while queued or running, or the request's error. */
 ds_status ds_poll(ds_ctx *ctx, uint64_t ticket, ds_result_info *info);
 /* Block up to timeout_s seconds; DS_ERR_TIMEOUT if still running. */
 ds_status ds_wait(ds_ctx *ctx, uint64_t ticket, double timeout_s, ds_result_info *info);
+
+/* Hold (pause = 1) or resume (0) admission of queued requests; requests already on the GPU
+ * continue.  Used to drain a context and by tests of bounded waits (no counterpart in the
+ * paper). */
+ds_status ds_serving_pause(ds_ctx *ctx, int pause);
 
 /* Adjoint: given dL/dI on `grid` (same layout and type as the intensity), write dL/du
  * (displacive) or dL/dM (magnetic) in the upload layout [model][site][n1][n2][n3][3] (type of

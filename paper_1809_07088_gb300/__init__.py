@@ -88,6 +88,9 @@ class Context:
         st = self.lib.ds_poll(self.h, C.c_uint64(ticket), C.byref(info))
         return st, info
 
+    def pause_serving(self, pause=True):
+        self.check(self.lib.ds_serving_pause(self.h, 1 if pause else 0))
+
     def wait(self, ticket, timeout_s=60.0):
         info = ds_result_info()
         self.check(self.lib.ds_wait(self.h, C.c_uint64(ticket), C.c_double(timeout_s), C.byref(info)))

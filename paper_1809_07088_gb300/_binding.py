@@ -36,7 +36,7 @@ class ds_opts(C.Structure):
 class ds_result_info(C.Structure):
     _fields_ = [("taylor_order", C.c_int), ("n_monomials", C.c_int), ("x_max", C.c_double),
                 ("trunc_bound", C.c_double), ("nvox", C.c_int64), ("workspace_bytes", C.c_int64),
-                ("gpu_ms", C.c_double)]
+                ("gpu_ms", C.c_double), ("latency_ms", C.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -65,6 +65,7 @@ SIGNATURES = {
     "ds_poll": (st, [vp, C.c_uint64, C.POINTER(ds_result_info)]),
     "ds_wait": (st, [vp, C.c_uint64, C.c_double, C.POINTER(ds_result_info)]),
     "ds_backward": (st, [vp, C.POINTER(ds_qgrid), C.POINTER(ds_opts), vp, vp, C.c_int, vp]),
+    "ds_serving_pause": (st, [vp, C.c_int]),
     "ds_profile_enable": (st, [vp, C.c_int]),
     "ds_profile_report": (st, [vp, C.c_char_p, C.c_size_t]),
     "ds_occupancy_intensity_noalloc": (st, [C.POINTER(C.c_double), C.c_int, vp, vp, C.c_int, C.c_int, C.c_int,

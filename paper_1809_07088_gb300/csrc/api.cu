@@ -568,6 +568,67 @@ void box_corners(const ds_model *M, const int g0[3], const int cnt[3], double co
             }
 }
 
+// smallest order whose remainder bound x_max^(P+1)/(P+1)! <= eps over the computing grid
+// (the requested grid plus the Lanczos halo); reads x_max back from the device (synchronises st)
+ds_status resolve_taylor_order(ds_model *M, const ds_qgrid *q, const ds_opts *o, cudaStream_t st, Scratch &ws, int *P,
+                               double *xmax) {
+    ds_ctx *ctx = M->ctx;
+    int g0[3], cnt[3];
+    ds_status rc = grid_indices(ctx, M, q, g0, cnt);
+    if (rc != DS_OK) return rc;
+    const int halo = o->smoothing == DS_SMOOTH_LANCZOS ? lanczos_halo(o->lanczos_m, o->lanczos_mprime) : 0;
+    int eg0[3], ecnt[3];
+    for (int a = 0; a < 3; ++a) {
+        eg0[a] = g0[a] - halo;
+        ecnt[a] = cnt[a] + 2 * halo;
+    }
+    Corners corners;
+    box_corners(M, eg0, ecnt, corners.v);
+    double *d_x = (double *)ws.get(sizeof(double) * 8);
+    if (ws.failed) return ds_fail(ctx, DS_ERR_OOM, "device allocation failed");
+    const size_t natom = (size_t)M->nmodels * M->nsite * M->n[0] * M->n[1] * M->n[2];
+    corner_xmax((int)natom, M->d_disp, corners, d_x, st);
+    double hx[8];
+    CK(cudaMemcpyAsync(hx, d_x, sizeof(hx), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    double x = 0.0;
+    for (int c = 0; c < 8; ++c) x = std::max(x, hx[c]);
+    *xmax = x;
+    *P = taylor_order_for(x, o->taylor_eps);
+    if (*P < 0 || *P > 60) return ds_fail(ctx, DS_ERR_UNSUPPORTED, "Taylor order above 60 (x_max = %g)", x);
+    return DS_OK;
+}
+
+// device bytes a request takes from the pool (the caller's output excluded); P = Taylor order
+size_t request_footprint(const ds_model *M, const ds_qgrid *q, const ds_opts *o, int P) {
+    Geometry g;
+    make_geometry(M->n, g);
+    const size_t es = o->precision == DS_FP64 ? 8 : 4, ce = 2 * es;
+    const size_t nsite = M->nsite, nmod = M->nmodels;
+    size_t cnt[3];
+    for (int a = 0; a < 3; ++a) cnt[a] = (size_t)q->count[a];
+    size_t bytes = 64 * 1024;  // tables
+    if (o->smoothing == DS_SMOOTH_SUBBOX) {
+        const size_t nf = nsite * (o->disorder == DS_SPIN ? 3 : 1), npair = nf * (nf + 1) / 2;
+        bytes += nmod * nf * g.ncell * es + npair * g.ncell * es + 2 * npair * g.ncell_h * ce;
+        return bytes;
+    }
+    size_t nf = nmod * nsite;
+    if (o->disorder == DS_SPIN) nf *= 3;
+    if (o->disorder == DS_DISP) {
+        const size_t T = (size_t)(P + 1) * (P + 2) * (P + 3) / 6;
+        nf *= T;
+        bytes += nmod * nsite * g.ncell * 3 * (P + 1) * es;
+    }
+    const size_t fb = std::max<size_t>(1, std::min<size_t>(nf, (512ull << 20) / (ce * g.ncell_h)));
+    bytes += (nf + fb) * g.ncell_h * ce;
+    if (o->smoothing == DS_SMOOTH_LANCZOS) {
+        const int h = lanczos_halo(o->lanczos_m, o->lanczos_mprime);
+        bytes += 3 * (cnt[0] + 2 * h) * (cnt[1] + 2 * h) * (cnt[2] + 2 * h) * es;
+    }
+    return bytes;
+}
+
 template <typename T>
 ds_status plan_and_run(ds_model *M, const ds_qgrid *q, const ds_opts *o, T *d_out, cudaStream_t st, Scratch &ws,
                        ds_result_info *info, ForwardKeep<T> *keep) {
@@ -660,16 +721,8 @@ ds_status plan_and_run(ds_model *M, const ds_qgrid *q, const ds_opts *o, T *d_ou
         if (!(qscale > 0)) qscale = 1.0;
         P = o->taylor_order;
         if (P < 0) {
-            double *d_x = (double *)ws.get(sizeof(double) * 8);
-            if (ws.failed) return ds_fail(ctx, DS_ERR_OOM, "device allocation failed");
-            corner_xmax((int)natom, M->d_disp, corners, d_x, st);
-            double hx[8];
-            CK(cudaMemcpyAsync(hx, d_x, sizeof(hx), cudaMemcpyDeviceToHost, st));
-            CK(cudaStreamSynchronize(st));
-            xmax = 0.0;
-            for (int c = 0; c < 8; ++c) xmax = std::max(xmax, hx[c]);
-            P = taylor_order_for(xmax, o->taylor_eps);
-            if (P < 0 || P > 60) return ds_fail(ctx, DS_ERR_UNSUPPORTED, "Taylor order above 60 (x_max = %g)", xmax);
+            rc = resolve_taylor_order(M, q, o, st, ws, &P, &xmax);
+            if (rc != DS_OK) return rc;
         }
         int4 *d_terms = nullptr;
         int *d_ops = nullptr;
@@ -762,23 +815,14 @@ ds_status plan_and_run(ds_model *M, const ds_qgrid *q, const ds_opts *o, T *d_ou
     return DS_OK;
 }
 
+// the request's kernels on stream st into the device volume d_out (no synchronisation)
 template <typename T>
-static ds_status run_intensity(ds_model *M, const ds_qgrid *q, const ds_opts *o, void *out, int out_dev,
-                               cudaStream_t st, ds_result_info *info) {
+ds_status enqueue_request(ds_model *M, const ds_qgrid *q, const ds_opts *o, T *d_out, cudaStream_t st, Scratch &ws,
+                          ds_result_info *info) {
     ds_ctx *ctx = M->ctx;
     int g0[3], cnt[3];
     ds_status rc = grid_indices(ctx, M, q, g0, cnt);
     if (rc != DS_OK) return rc;
-    const size_t nvox = (size_t)cnt[0] * cnt[1] * cnt[2];
-    Scratch ws(st);
-    cudaEvent_t e0 = nullptr, e1 = nullptr;
-    if (!out_dev) {
-        CK(cudaEventCreate(&e0));
-        CK(cudaEventCreate(&e1));
-        CK(cudaEventRecord(e0, st));
-    }
-    T *d_out = out_dev ? (T *)out : (T *)ws.get(sizeof(T) * nvox);
-    if (!d_out) return ds_fail(ctx, DS_ERR_OOM, "device allocation failed (output)");
     if (o->smoothing == DS_SMOOTH_SUBBOX) {
         rc = subbox_run<T>(M, q, o, d_out, st, ws, info);
     } else if (o->smoothing == DS_SMOOTH_LANCZOS) {
@@ -796,29 +840,49 @@ static ds_status run_intensity(ds_model *M, const ds_qgrid *q, const ds_opts *o,
     } else {
         rc = plan_and_run<T>(M, q, o, d_out, st, ws, info, nullptr);
     }
-    if (rc != DS_OK) {
-        ws.release();
-        cudaStreamSynchronize(st);
-        return rc;
-    }
-    if (info) {
-        info->nvox = (int64_t)nvox;
+    if (rc == DS_OK && info) {
+        info->nvox = (int64_t)cnt[0] * cnt[1] * cnt[2];
         info->workspace_bytes = (int64_t)ws.total;
-        info->gpu_ms = 0.0;
     }
+    return rc;
+}
+
+template <typename T>
+static ds_status run_intensity(ds_model *M, const ds_qgrid *q, const ds_opts *o, void *out, int out_dev,
+                               cudaStream_t st, ds_result_info *info) {
+    ds_ctx *ctx = M->ctx;
+    int g0[3], cnt[3];
+    ds_status rc = grid_indices(ctx, M, q, g0, cnt);
+    if (rc != DS_OK) return rc;
+    const size_t nvox = (size_t)cnt[0] * cnt[1] * cnt[2];
+    Scratch ws(st);
+    T *d_out = out_dev ? (T *)out : (T *)ws.get(sizeof(T) * nvox);
+    if (!d_out) return ds_fail(ctx, DS_ERR_OOM, "device allocation failed (output)");
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (!out_dev) {
-        CK(cudaEventRecord(e1, st));
-        CK(cudaMemcpyAsync(out, d_out, sizeof(T) * nvox, cudaMemcpyDeviceToHost, st));
-        ws.release();
-        CK(cudaStreamSynchronize(st));
+        CK(cudaEventCreate(&e0));
+        CK(cudaEventCreate(&e1));
+        cudaEventRecord(e0, st);
+    }
+    if (info) info->gpu_ms = 0.0;
+    rc = enqueue_request<T>(M, q, o, d_out, st, ws, info);
+    if (rc == DS_OK && !out_dev) {
+        cudaEventRecord(e1, st);
+        if (cudaMemcpyAsync(out, d_out, sizeof(T) * nvox, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+            rc = ds_fail(ctx, DS_ERR_CUDA, "copy of the volume to the host failed");
+    }
+    ws.release();
+    if (!out_dev || rc != DS_OK) {
+        if (cudaStreamSynchronize(st) != cudaSuccess && rc == DS_OK)
+            rc = ds_fail(ctx, DS_ERR_CUDA, "stream synchronisation failed: %s", cudaGetErrorString(cudaGetLastError()));
+    }
+    if (e0) {
         float ms = 0.f;
-        cudaEventElapsedTime(&ms, e0, e1);
-        if (info) info->gpu_ms = ms;
+        if (rc == DS_OK && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess && info) info->gpu_ms = ms;
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
-    } else {
-        ws.release();
     }
+    if (rc != DS_OK) return rc;
     CK(cudaGetLastError());
     return DS_OK;
 }
@@ -928,3 +992,8 @@ extern "C" ds_status ds_profile_report(ds_ctx *ctx, char *json, size_t cap) {
     if (rc != DS_OK) return ds_fail(ctx, rc, "event timing failed");
     return DS_OK;
 }
+
+template ds_status enqueue_request<float>(ds_model *, const ds_qgrid *, const ds_opts *, float *, cudaStream_t,
+                                          Scratch &, ds_result_info *);
+template ds_status enqueue_request<double>(ds_model *, const ds_qgrid *, const ds_opts *, double *, cudaStream_t,
+                                           Scratch &, ds_result_info *);

@@ -72,6 +72,7 @@ struct ds_ctx {
     std::thread worker;
     bool worker_started = false;
     bool stop = false;
+    bool paused = false;
     uint64_t next_ticket = 1;
     std::deque<ServeJob *> queue;
     std::map<uint64_t, ServeJob *> jobs;
@@ -127,6 +128,13 @@ void box_corners(const ds_model *M, const int g0[3], const int cnt[3], double co
 template <typename T>
 ds_status plan_and_run(ds_model *M, const ds_qgrid *q, const ds_opts *o, T *d_out, cudaStream_t st, Scratch &ws,
                        ds_result_info *info, ForwardKeep<T> *keep);
+// all kernels of one request into a device volume, no synchronisation (smoothing included)
+template <typename T>
+ds_status enqueue_request(ds_model *M, const ds_qgrid *q, const ds_opts *o, T *d_out, cudaStream_t st, Scratch &ws,
+                          ds_result_info *info);
+ds_status resolve_taylor_order(ds_model *M, const ds_qgrid *q, const ds_opts *o, cudaStream_t st, Scratch &ws, int *P,
+                               double *xmax);
+size_t request_footprint(const ds_model *M, const ds_qgrid *q, const ds_opts *o, int P);
 // sub-box averaging (subbox.cu)
 template <typename T>
 ds_status subbox_run(ds_model *M, const ds_qgrid *q, const ds_opts *o, T *d_out, cudaStream_t st, Scratch &ws,
