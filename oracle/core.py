@@ -359,7 +359,41 @@ def taylor_order(xmax: float, eps: float) -> int:
     return P
 
 
-def displacive_intensity_fft(model, G, mode=DIFFUSE, P=None, eps=1e-8, return_F=False):
+def zone_taylor_orders(model, qgrid, eps: float, G=None):
+    """Taylor order per voxel under the per-zone reading of the remainder bound of Section
+    III C, and the single order P of the whole grid.
+
+    A zone is the set of grid voxels G = n H + k sharing one H = floor(G / n).  By
+    Cauchy-Schwarz |Q . u_j| <= |Q| |u_j|, so over a zone max_j |Q . u_j| <= x_H =
+    min(q_H u_max, x_max), with q_H the largest |Q| over the zone's voxels (|Q| is convex, so it
+    is reached at a corner of the zone's box of voxels) and u_max the largest |u_j| of the
+    ensemble.  The zone's order is the smallest order whose bound x_H^(P+1)/(P+1)! <= eps,
+    never above P.  Returns (orders, P): orders [nvox] for every voxel of the grid, or for the
+    voxels G [nq, 3] (supercell indices inside the grid) when given."""
+    n = np.asarray(model.cells, dtype=np.int64)
+    glo = np.rint(np.asarray(qgrid.h0) * n).astype(np.int64)
+    ghi = glo + np.asarray(qgrid.count, dtype=np.int64) - 1
+    xm = x_max(model, qgrid)
+    P = taylor_order(xm, eps)
+    u = model.disp.reshape(-1, 3).astype(np.float64)
+    umax = float(np.max(np.sqrt(np.sum(u * u, axis=1))))
+    Hlo, Hhi = np.floor_divide(glo, n), np.floor_divide(ghi, n)
+    nH = Hhi - Hlo + 1
+    table = np.empty(tuple(nH), dtype=np.int64)
+    for h in np.ndindex(*table.shape):
+        Hz = Hlo + np.array(h)
+        lo = np.maximum(n * Hz, glo)
+        hi = np.minimum(n * Hz + n - 1, ghi)
+        box = np.array([[(hi if (c >> (2 - a)) & 1 else lo)[a] for a in range(3)] for c in range(8)])
+        qmax = float(np.max(np.linalg.norm(q_cart(box / n[None, :], model.lattice), axis=1)))
+        table[h] = min(P, taylor_order(min(qmax * umax, xm), eps))
+    if G is None:
+        G = qgrid.g_index(model.cells)
+    h = np.floor_divide(np.asarray(G, dtype=np.int64), n[None, :]) - Hlo[None, :]
+    return table[h[:, 0], h[:, 1], h[:, 2]], P
+
+
+def displacive_intensity_fft(model, G, mode=DIFFUSE, P=None, eps=1e-8, return_F=False, P_vox=None):
     """Taylor-expanded FFT method, Eqs. disp_expansion, gu_expansion, total_sf_taylor, U_fft,
     A_fft, bragg_sf_disp, disp_diffuse_intensity.
 
@@ -369,9 +403,12 @@ def displacive_intensity_fft(model, G, mode=DIFFUSE, P=None, eps=1e-8, return_F=
     collapse into the multinomial weight n!/(a! b! c!), so the term's coefficient is
     i^n Q_x^a Q_y^b Q_z^c / (a! b! c!) with Q Cartesian and u in Angstrom.  The Bragg term keeps
     the even orders of the k = 0 transforms averaged over the supercells.  Streaming over
-    monomials keeps the memory at one field at a time."""
+    monomials keeps the memory at one field at a time.  P_vox (optional, [nvox]): the order of
+    each voxel (zone orders); each voxel then keeps only its monomials of order n <= P_vox, the
+    Bragg term included; P must be at least max(P_vox)."""
     if P is None:
         raise ValueError("pass the Taylor order P")
+    keep_n = None if P_vox is None else np.asarray(P_vox)[None, :] >= np.arange(P + 1)[:, None]  # [n][nvox]
     k = split_G(G, model.cells)
     phi, Q = _phi(model, G)
     nv = G.shape[0]
@@ -394,6 +431,8 @@ def displacive_intensity_fft(model, G, mode=DIFFUSE, P=None, eps=1e-8, return_F=
             Mk = lattice_fft(field)[:, k[:, 0], k[:, 1], k[:, 2]]            # [model][nvox]
             coef = (1j ** n) * pw[0][:, a] * pw[1][:, b] * pw[2][:, c] / (
                 math.factorial(a) * math.factorial(b) * math.factorial(c))
+            if keep_n is not None:
+                coef = np.where(keep_n[n], coef, 0.0)
             S += coef[None, :] * Mk
             if mode == DIFFUSE and n % 2 == 0:
                 Sb += coef * np.mean(Mk, axis=0)
@@ -405,15 +444,15 @@ def displacive_intensity_fft(model, G, mode=DIFFUSE, P=None, eps=1e-8, return_F=
     return (I, F) if return_F else I
 
 
-def truncation_bound(model, hkl, P: int, mode=DIFFUSE, F=None, chunk=4096):
+def truncation_bound(model, hkl, P, mode=DIFFUSE, F=None, chunk=4096):
     """Voxel-wise bound on |I_P - I| from the remainder |x|^(P+1)/(P+1)! of each atom's
     exp(i Q.u) (Section III C): dF = sum_j |w_j f_j| |Q.u_j|^(P+1)/(P+1)!; the Bragg term adds
     the supercell-mean of the same bound at integer H; then |I_P - I| <= (2|F| d + d^2)/N
     averaged over supercells, with F the exact (direct-sum) structure factor minus <F>.
-    Evaluated in chunks of Q points to bound memory."""
+    P is one order or one per Q point.  Evaluated in chunks of Q points to bound memory."""
     _, site = atom_list(model)
-    lf = math.lgamma(P + 2)
     nq = hkl.shape[0]
+    Pq = np.broadcast_to(np.asarray(P, dtype=np.float64), (nq,))
     dFs = np.zeros((model.nmodels, nq))
     for s0 in range(0, nq, chunk):
         h = hkl[s0:s0 + chunk]
@@ -426,7 +465,9 @@ def truncation_bound(model, hkl, P: int, mode=DIFFUSE, F=None, chunk=4096):
             u = model.disp[m].reshape(-1, 3).astype(np.float64)
             w = np.abs(displacive_weights(model, m))
             x = np.abs(Q @ u.T)                             # [nq, natom]
-            rem = np.exp((P + 1) * np.log(np.maximum(x, 1e-300)) - lf)
+            Pc = Pq[s0:s0 + chunk][:, None]
+            lf = np.array([math.lgamma(v + 2) for v in Pc[:, 0]])[:, None]
+            rem = np.exp((Pc + 1) * np.log(np.maximum(x, 1e-300)) - lf)
             dFs[m, s0:s0 + chunk] = np.sum(ff * w[None, :] * rem, axis=1)
     if mode == DIFFUSE:
         dFs = dFs + is_integer_hkl(hkl)[None, :] * dFs.mean(axis=0)[None, :]

@@ -298,6 +298,44 @@ def test_taylor_order_and_x_max():
     assert math.isclose(core.x_max(m, m.qgrid), float(np.max(np.abs(Q @ u.T))), rel_tol=1e-12)
 
 
+def test_zone_taylor_orders_bound_every_voxel():
+    """Per-zone reading of the remainder bound (Section III C): at every voxel the zone's order
+    keeps the largest per-atom remainder |Q.u_j|^(P+1)/(P+1)! (brute force over all atoms) below
+    eps; no zone exceeds the grid order, the zone of largest |Q| takes it when the bound
+    |Q||u| is tight enough, and the zones near Q = 0 take a lower one."""
+    m = syn.small_case(syn.DISP, cells=(3, 4, 2), nsite=3, nmodels=2, seed=33, sigma=0.15)
+    eps = 1e-6
+    pv, P = core.zone_taylor_orders(m, m.qgrid, eps)
+    Q = core.q_cart(m.qgrid.hkl(), m.lattice)
+    u = m.disp.reshape(-1, 3).astype(np.float64)
+    x = np.max(np.abs(Q @ u.T), axis=1)                      # per voxel, all atoms
+    lf = np.array([math.lgamma(p + 2) for p in pv])
+    assert np.all((pv + 1) * np.log(np.maximum(x, 1e-300)) - lf <= math.log(eps) + 1e-12)
+    assert pv.max() <= P and pv.min() < P
+    qn = np.linalg.norm(Q, axis=1)
+    assert pv[np.argmin(qn)] < pv[np.argmax(qn)]
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_zone_orders_equal_fixed_order_per_voxel(mode):
+    """Masking by zone order: each voxel of the per-zone result equals the fixed-order method
+    run at that voxel's own order (a separate run per order, Bragg term included), and stays
+    within the per-voxel remainder bound of the exact direct sum."""
+    m = syn.small_case(syn.DISP, cells=(3, 4, 2), nsite=3, nmodels=2, seed=34, sigma=0.15)
+    pv, P = core.zone_taylor_orders(m, m.qgrid, 1e-5)
+    G = _grid_G(m)
+    I_z = core.displacive_intensity_fft(m, G, mode, P=P, P_vox=pv)
+    assert len(np.unique(pv)) >= 2
+    for p in np.unique(pv):
+        sel = pv == p
+        I_p = core.displacive_intensity_fft(m, G[sel], mode, P=int(p))
+        assert np.allclose(I_z[sel], I_p, rtol=1e-12, atol=1e-13 * np.abs(I_z).max())
+    hkl = G / np.array(m.cells)
+    I_dir, F = core.displacive_intensity_direct(m, hkl, mode, return_F=True)
+    bound = core.truncation_bound(m, hkl, pv, mode, F=F)
+    assert np.all(np.abs(I_z - I_dir) <= bound * (1 + 1e-9) + 1e-12 * I_dir.max())
+
+
 def test_gaussian_displacements_laue_closed_form():
     """Independent Gaussian displacements (sigma per Cartesian component), f = 1: at every
     k != 0 voxel E[I] = 1 - exp(-Q^2 sigma^2); at allowed unit-cell Bragg positions the total
