@@ -87,6 +87,10 @@ typedef struct {
     int lanczos_m;      /* m >= 2 of Eq. lanczos */
     int lanczos_mprime; /* m' >= 2 (2 = the plain window; r_cut = (1 - 1/m)/m') */
     int subbox_n;       /* n_sb of Section V A, 1 <= n_sb <= n_alpha/2 */
+    int taylor_zonal;   /* displacive with taylor_order < 0: 1 = an order per zone H of the
+                           grid, from x_H = min(max_zone |Q| * max_j |u_j|, x_max), so that the
+                           same remainder bound holds at every voxel (|Q.u| <= |Q||u|); 0 = one
+                           order for the whole grid.  Not accepted by ds_backward. */
 } ds_opts;
 
 typedef struct {

@@ -200,6 +200,7 @@ static bool form_factor_classes(const ds_model *M, std::vector<int> &site_of, Fo
             const int s = site_of[i];
             ff.cls_kind[ff.ncls] = M->ffkind[s];
             for (int j = 0; j < 9; ++j) ff.cls_coef[ff.ncls][j] = (T)M->ffcoef[9 * s + j];
+            gaussian_sum_form(ff, ff.ncls, M->ffkind[s], &M->ffcoef[9 * s]);
             ff.ncls++;
         }
         ff.cls_end[ff.ncls - 1] = i + 1;
@@ -295,15 +296,27 @@ extern "C" ds_status ds_model_create(ds_ctx *ctx, ds_model **out) {
     return DS_OK;
 }
 
+static void clear_site_tables(ds_model *m) {
+    for (auto &kv : m->site_tables) {
+        cudaFree(kv.second.phk);
+        cudaFree(kv.second.phH);
+        cudaEventDestroy(kv.second.done);
+    }
+    m->site_tables.clear();
+}
+
 static void free_arrays(ds_model *m) {
     cudaSetDevice(m->ctx->device);
     cudaDeviceSynchronize();
-    if (m->d_occ) cudaFree(m->d_occ);
-    if (m->d_spins) cudaFree(m->d_spins);
-    if (m->d_disp) cudaFree(m->d_disp);
+    for (void *p : {(void *)m->d_occ, (void *)m->d_spins, (void *)m->d_disp, (void *)m->d_mean_occ,
+                    (void *)m->d_mean_spin})
+        if (p) cudaFree(p);
     m->d_occ = nullptr;
     m->d_spins = nullptr;
     m->d_disp = nullptr;
+    m->d_mean_occ = nullptr;
+    m->d_mean_spin = nullptr;
+    clear_site_tables(m);
 }
 
 static void free_constants(ds_model *m) {
@@ -320,6 +333,9 @@ static void free_constants(ds_model *m) {
         cudaFree(kv.second.second);
     }
     m->taylor_tables.clear();
+    for (auto &kv : m->sub_tables) cudaFree(kv.second);
+    m->sub_tables.clear();
+    clear_site_tables(m);
 }
 
 static void free_twiddles(ds_model *m) {
@@ -336,6 +352,7 @@ extern "C" ds_status ds_model_destroy(ds_model *m) {
     free_arrays(m);
     free_constants(m);
     free_twiddles(m);
+    if (m->ready) cudaEventDestroy(m->ready);
     if (m->d_sites) cudaFree(m->d_sites);
     m->ctx->models.erase(m);
     delete m;
@@ -411,6 +428,18 @@ extern "C" ds_status ds_model_set_sites(ds_model *m, int nsite, const double *xy
         G.cls_grp_end[cls] = G.ngrp;
         for (int c = cls + 1; c < MAX_FF_CLASSES; ++c) G.cls_grp_end[c] = -1;
     }
+    // periods of the zone phases exp(2 pi i H_a r_mu,a): every coordinate a multiple of 1/d
+    for (int a = 0; a < 3; ++a) {
+        m->period[a] = 0;
+        for (int d = 1; d <= 64 && !m->period[a]; ++d) {
+            bool ok = true;
+            for (int i = 0; i < nsite && ok; ++i) {
+                const double x = d * m->sites[3 * i + a];
+                ok = fabs(x - rint(x)) <= 1e-13;
+            }
+            if (ok) m->period[a] = d;
+        }
+    }
     std::vector<float> s32(nsite);
     for (int i = 0; i < nsite; ++i) s32[i] = (float)m->scat[i];
     CK(cudaMalloc(&m->d_site_of, sizeof(int) * nsite));
@@ -419,6 +448,46 @@ extern "C" ds_status ds_model_set_sites(ds_model *m, int nsite, const double *xy
     CK(cudaMemcpy(m->d_site_of, m->site_of.data(), sizeof(int) * nsite, cudaMemcpyHostToDevice));
     CK(cudaMemcpy(m->d_scat32, s32.data(), sizeof(float) * nsite, cudaMemcpyHostToDevice));
     CK(cudaMemcpy(m->d_scat64, m->scat.data(), sizeof(double) * nsite, cudaMemcpyHostToDevice));
+    return DS_OK;
+}
+
+// for every order p <= P, the lexicographic monomials of order <= p as indices into the order-P
+// list, with their coefficient update codes: [map | ops | off[P+2]] on the device, per model
+static ds_status sub_simplex_tables(ds_model *m, int P, int **tab) {
+    ds_ctx *ctx = m->ctx;
+    auto it = m->sub_tables.find(P);
+    if (it != m->sub_tables.end()) {
+        *tab = it->second;
+        return DS_OK;
+    }
+    std::vector<int4> terms;
+    std::vector<int> ops;
+    monomial_tables(P, terms, ops);
+    std::map<long long, int> index;
+    for (size_t t = 0; t < terms.size(); ++t)
+        index[((long long)terms[t].x * 1024 + terms[t].y) * 1024 + terms[t].z] = (int)t;
+    std::vector<int> map, sops, off;
+    for (int p = 0; p <= P; ++p) {
+        off.push_back((int)map.size());
+        std::vector<int4> tp;
+        std::vector<int> op;
+        monomial_tables(p, tp, op);
+        for (size_t t = 0; t < tp.size(); ++t) {
+            map.push_back(index[((long long)tp[t].x * 1024 + tp[t].y) * 1024 + tp[t].z]);
+            sops.push_back(op[t]);
+        }
+    }
+    off.push_back((int)map.size());
+    const size_t n = map.size();
+    std::vector<int> all(2 * n + off.size());
+    std::copy(map.begin(), map.end(), all.begin());
+    std::copy(sops.begin(), sops.end(), all.begin() + n);
+    for (size_t i = 0; i < off.size(); ++i) all[2 * n + i] = off[i];
+    int *d = nullptr;
+    CK(cudaMalloc(&d, sizeof(int) * all.size()));
+    CK(cudaMemcpy(d, all.data(), sizeof(int) * all.size(), cudaMemcpyHostToDevice));
+    m->sub_tables[P] = d;
+    *tab = d;
     return DS_OK;
 }
 
@@ -480,6 +549,15 @@ static ds_status upload(ds_model *m, void **dst, const void *src, size_t bytes, 
     cudaStream_t st = (cudaStream_t)stream;
     if (!*dst) CK(cudaMalloc(dst, bytes));
     CK(cudaMemcpyAsync(*dst, src, bytes, src_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+    return DS_OK;
+}
+
+// after an upload on stream st: mark the model's data ready for requests on any stream, and wait
+// for host sources (their memory may be reused by the caller on return)
+static ds_status upload_done(ds_model *m, int src_dev, cudaStream_t st) {
+    ds_ctx *ctx = m->ctx;
+    if (!m->ready) CK(cudaEventCreateWithFlags(&m->ready, cudaEventDisableTiming));
+    CK(cudaEventRecord(m->ready, st));
     if (!src_dev) CK(cudaStreamSynchronize(st));
     return DS_OK;
 }
@@ -491,29 +569,39 @@ extern "C" ds_status ds_model_upload_occupancy(ds_model *m, const uint8_t *occ, 
     if (!m) return DS_ERR_ARG;
     ds_status st = upload(m, (void **)&m->d_occ, occ, natoms(m), src_dev, stream);
     if (st != DS_OK) return st;
+    ds_ctx *ctx = m->ctx;
+    cudaStream_t cs = (cudaStream_t)stream;
     m->has_occ = true;
     m->user_mean = mean != nullptr;
     if (mean) {
-        ds_ctx *ctx = m->ctx;
         m->mean_occ.assign(mean, mean + m->nsite);
         if (!m->d_user_mean) CK(cudaMalloc(&m->d_user_mean, sizeof(double) * m->nsite));
         CK(cudaMemcpy(m->d_user_mean, mean, sizeof(double) * m->nsite, cudaMemcpyHostToDevice));
     }
-    return DS_OK;
+    // sample means c_mu over lattice points and supercells (Eq. occ), once per upload
+    if (!m->d_mean_occ) CK(cudaMalloc(&m->d_mean_occ, sizeof(double) * m->nsite));
+    site_means_occ(m->nmodels, m->nsite, m->n[0] * m->n[1] * m->n[2], m->d_occ, m->d_mean_occ, cs);
+    return upload_done(m, src_dev, cs);
 }
 
 extern "C" ds_status ds_model_upload_spins(ds_model *m, const float *spins, int src_dev, void *stream) {
     if (!m) return DS_ERR_ARG;
     ds_status st = upload(m, (void **)&m->d_spins, spins, natoms(m) * 3 * sizeof(float), src_dev, stream);
-    if (st == DS_OK) m->has_spins = true;
-    return st;
+    if (st != DS_OK) return st;
+    ds_ctx *ctx = m->ctx;
+    cudaStream_t cs = (cudaStream_t)stream;
+    m->has_spins = true;
+    if (!m->d_mean_spin) CK(cudaMalloc(&m->d_mean_spin, sizeof(double) * 3 * m->nsite));
+    site_means_spin(m->nmodels, m->nsite, m->n[0] * m->n[1] * m->n[2], m->d_spins, m->d_mean_spin, cs);
+    return upload_done(m, src_dev, cs);
 }
 
 extern "C" ds_status ds_model_upload_displacements(ds_model *m, const float *disp, int src_dev, void *stream) {
     if (!m) return DS_ERR_ARG;
     ds_status st = upload(m, (void **)&m->d_disp, disp, natoms(m) * 3 * sizeof(float), src_dev, stream);
-    if (st == DS_OK) m->has_disp = true;
-    return st;
+    if (st != DS_OK) return st;
+    m->has_disp = true;
+    return upload_done(m, src_dev, (cudaStream_t)stream);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -545,6 +633,7 @@ ds_status check_request(ds_model *M, const ds_qgrid *q, const ds_opts *o) {
     if (o->disorder == DS_DISP && o->taylor_order < 0 && !(o->taylor_eps > 0 && o->taylor_eps < 1))
         return ds_fail(ctx, DS_ERR_ARG, "taylor_eps must be in (0, 1) when taylor_order < 0");
     if (o->disorder == DS_DISP && o->taylor_order > 60) return ds_fail(ctx, DS_ERR_UNSUPPORTED, "taylor_order > 60");
+    if (o->taylor_zonal != 0 && o->taylor_zonal != 1) return ds_fail(ctx, DS_ERR_ARG, "taylor_zonal must be 0 or 1");
     if (o->disorder != DS_DISP && M->nsite > 32 && o->disorder == DS_OCC)
         return ds_fail(ctx, DS_ERR_UNSUPPORTED, "occupancy recombination handles up to 32 sites");
     if (o->disorder == DS_SPIN && M->nsite > 16)
@@ -571,7 +660,7 @@ void box_corners(const ds_model *M, const int g0[3], const int cnt[3], double co
 // smallest order whose remainder bound x_max^(P+1)/(P+1)! <= eps over the computing grid
 // (the requested grid plus the Lanczos halo); reads x_max back from the device (synchronises st)
 ds_status resolve_taylor_order(ds_model *M, const ds_qgrid *q, const ds_opts *o, cudaStream_t st, Scratch &ws, int *P,
-                               double *xmax) {
+                               double *xmax, double *umax) {
     ds_ctx *ctx = M->ctx;
     int g0[3], cnt[3];
     ds_status rc = grid_indices(ctx, M, q, g0, cnt);
@@ -584,16 +673,18 @@ ds_status resolve_taylor_order(ds_model *M, const ds_qgrid *q, const ds_opts *o,
     }
     Corners corners;
     box_corners(M, eg0, ecnt, corners.v);
-    double *d_x = (double *)ws.get(sizeof(double) * 8);
+    if (M->ready) CK(cudaStreamWaitEvent(st, M->ready, 0));
+    double *d_x = (double *)ws.get(sizeof(double) * 9);
     if (ws.failed) return ds_fail(ctx, DS_ERR_OOM, "device allocation failed");
     const size_t natom = (size_t)M->nmodels * M->nsite * M->n[0] * M->n[1] * M->n[2];
     corner_xmax((int)natom, M->d_disp, corners, d_x, st);
-    double hx[8];
+    double hx[9];
     CK(cudaMemcpyAsync(hx, d_x, sizeof(hx), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     double x = 0.0;
     for (int c = 0; c < 8; ++c) x = std::max(x, hx[c]);
     *xmax = x;
+    if (umax) *umax = hx[8];
     *P = taylor_order_for(x, o->taylor_eps);
     if (*P < 0 || *P > 60) return ds_fail(ctx, DS_ERR_UNSUPPORTED, "Taylor order above 60 (x_max = %g)", x);
     return DS_OK;
@@ -629,14 +720,55 @@ size_t request_footprint(const ds_model *M, const ds_qgrid *q, const ds_opts *o,
     return bytes;
 }
 
+// site phase tables exp(2 pi i k_a r_a / n_a) and exp(2 pi i H_a r_a) of a grid, cached per model
+// (at most 256 grids; beyond that they are rebuilt in request scratch); a stream that did not
+// build them waits for the building stream's kernel
+template <typename T>
+ds_status site_tables(ds_model *M, const Geometry &g, const GridMap &gm, int nmax, int nHmax, cudaStream_t st,
+                      Scratch &ws, const c_t<T> **phk, const c_t<T> **phH) {
+    using C = c_t<T>;
+    ds_ctx *ctx = M->ctx;
+    const std::vector<int> key = {(int)sizeof(T), gm.Hmin[0], gm.Hmin[1], gm.Hmin[2], gm.nH[0], gm.nH[1], gm.nH[2]};
+    const size_t bk = sizeof(C) * M->nsite * 3 * nmax, bh = sizeof(C) * M->nsite * 3 * nHmax;
+    std::lock_guard<std::mutex> lk(M->cache_mu);
+    auto it = M->site_tables.find(key);
+    if (it != M->site_tables.end()) {
+        CK(cudaStreamWaitEvent(st, it->second.done, 0));
+        *phk = (const C *)it->second.phk;
+        *phH = (const C *)it->second.phH;
+        return DS_OK;
+    }
+    C *k = nullptr, *h = nullptr;
+    if (M->site_tables.size() >= 256) {
+        k = (C *)ws.get(bk);
+        h = (C *)ws.get(bh);
+        if (ws.failed) return ds_fail(ctx, DS_ERR_OOM, "device allocation failed (tables)");
+        make_site_tables<T>(g, gm, M->nsite, M->d_sites, k, h, nmax, nHmax, st);
+    } else {
+        ds_model::SiteTables e;
+        CK(cudaMalloc(&e.phk, bk));
+        CK(cudaMalloc(&e.phH, bh));
+        CK(cudaEventCreateWithFlags(&e.done, cudaEventDisableTiming));
+        make_site_tables<T>(g, gm, M->nsite, M->d_sites, (C *)e.phk, (C *)e.phH, nmax, nHmax, st);
+        CK(cudaEventRecord(e.done, st));
+        M->site_tables[key] = e;
+        k = (C *)e.phk;
+        h = (C *)e.phH;
+    }
+    *phk = k;
+    *phH = h;
+    return DS_OK;
+}
+
 template <typename T>
 ds_status plan_and_run(ds_model *M, const ds_qgrid *q, const ds_opts *o, T *d_out, cudaStream_t st, Scratch &ws,
-                       ds_result_info *info, ForwardKeep<T> *keep) {
+                       ds_result_info *info, ForwardKeep<T> *keep, const TaylorHint *hint) {
     using C = c_t<T>;
     ds_ctx *ctx = M->ctx;
     int g0[3], cnt[3];
     ds_status rc = grid_indices(ctx, M, q, g0, cnt);
     if (rc != DS_OK) return rc;
+    if (M->ready) CK(cudaStreamWaitEvent(st, M->ready, 0));  // uploads made on another stream
     Geometry g;
     make_geometry(M->n, g);
     const int nsite = M->nsite, nmod = M->nmodels;
@@ -663,7 +795,15 @@ ds_status plan_and_run(ds_model *M, const ds_qgrid *q, const ds_opts *o, T *d_ou
     if constexpr (sizeof(T) == 4) p.ff = M->ff32;
     else p.ff = M->ff64;
     p.grp = M->groups;
-    memcpy(p.recip, M->recip, sizeof(p.recip));
+    if (o->disorder != DS_DISP) {
+        // residue classes of zones: used when they are at most half as many as the zones
+        int dres[3];
+        for (int a = 0; a < 3; ++a)
+            dres[a] = (M->period[a] > 0 && M->period[a] < gm.nH[a]) ? M->period[a] : gm.nH[a];
+        if (2LL * dres[0] * dres[1] * dres[2] <= (long long)gm.nH[0] * gm.nH[1] * gm.nH[2])
+            for (int a = 0; a < 3; ++a) p.dres[a] = dres[a];
+    }
+    set_reciprocal(p, M->recip, g.n);
     const double N = (double)nsite * g.ncell;
     p.norm = (T)(1.0 / (nmod * N));
     if (o->disorder == DS_SPIN) p.norm = (T)(0.07265 / (nmod * N));  // C of Eq. mag_intensity (barn)
@@ -671,18 +811,13 @@ ds_status plan_and_run(ds_model *M, const ds_qgrid *q, const ds_opts *o, T *d_ou
     // small tables: site phases of this grid (twiddles, site order and b are per model)
     p.nmax = std::max(g.n[0], std::max(g.n[1], g.n[2]));
     p.nHmax = std::max(gm.nH[0], std::max(gm.nH[1], gm.nH[2]));
-    C *phk = (C *)ws.get(sizeof(C) * nsite * 3 * p.nmax);
-    C *phH = (C *)ws.get(sizeof(C) * nsite * 3 * p.nHmax);
-    double *d_mean = (double *)ws.get(sizeof(double) * nsite * 3);
-    if (ws.failed) return ds_fail(ctx, DS_ERR_OOM, "device allocation failed (tables)");
     const C *W[3];
     for (int a = 0; a < 3; ++a) {
         if constexpr (sizeof(T) == 4) W[a] = M->d_tw32[a];
         else W[a] = M->d_tw64[a];
     }
-    make_site_tables<T>(g, gm, nsite, M->d_sites, phk, phH, p.nmax, p.nHmax, st);
-    p.phk = phk;
-    p.phH = phH;
+    rc = site_tables<T>(M, g, gm, p.nmax, p.nHmax, st, ws, &p.phk, &p.phH);
+    if (rc != DS_OK) return rc;
     p.site_of = M->d_site_of;
     p.sites = M->d_sites;
     if constexpr (sizeof(T) == 4) p.scat = M->d_scat32;
@@ -700,18 +835,13 @@ ds_status plan_and_run(ds_model *M, const ds_qgrid *q, const ds_opts *o, T *d_ou
         src.kind = SRC_OCC;
         src.occ = M->d_occ;
         nf_model = nsite;
-        src.mean = d_mean;
-        if (src.diffuse) {
-            if (M->user_mean) src.mean = M->d_user_mean;
-            else site_means_occ(nmod, nsite, g.ncell, M->d_occ, d_mean, st);
-        }
+        src.mean = M->user_mean ? M->d_user_mean : M->d_mean_occ;
         p.ncomp = 1;
     } else if (o->disorder == DS_SPIN) {
         src.kind = SRC_SPIN;
         src.vec3 = M->d_spins;
         nf_model = 3 * nsite;
-        if (src.diffuse) site_means_spin(nmod, nsite, g.ncell, M->d_spins, d_mean, st);
-        src.mean = d_mean;
+        src.mean = M->d_mean_spin;
         p.ncomp = 3;
     } else {
         Corners corners;
@@ -720,8 +850,14 @@ ds_status plan_and_run(ds_model *M, const ds_qgrid *q, const ds_opts *o, T *d_ou
         for (int i = 0; i < 24; ++i) qscale = std::max(qscale, fabs(corners.v[i]));
         if (!(qscale > 0)) qscale = 1.0;
         P = o->taylor_order;
-        if (P < 0) {
-            rc = resolve_taylor_order(M, q, o, st, ws, &P, &xmax);
+        double umax = 0.0;
+        const bool auto_order = P < 0;
+        if (auto_order && hint) {
+            P = hint->P;
+            xmax = hint->xmax;
+            umax = hint->umax;
+        } else if (auto_order) {
+            rc = resolve_taylor_order(M, q, o, st, ws, &P, &xmax, &umax);
             if (rc != DS_OK) return rc;
         }
         int4 *d_terms = nullptr;
@@ -743,6 +879,48 @@ ds_status plan_and_run(ds_model *M, const ds_qgrid *q, const ds_opts *o, T *d_ou
         p.ops = d_ops;
         p.terms = d_terms;
         p.qscale = qscale;
+        if (auto_order && o->taylor_zonal && P > 0) {
+            // Taylor order per zone: every voxel G of a zone has max_j |Q.u_j| <= min(|Q|max u_max,
+            // x_max) (Cauchy-Schwarz), so the remainder bound of Section III C holds there with the
+            // order of that smaller argument; |Q| is convex, its maximum over the zone's voxel box
+            // is at a corner
+            const int nz = gm.nH[0] * gm.nH[1] * gm.nH[2];
+            std::vector<int> pz(nz);
+            for (int h1 = 0; h1 < gm.nH[0]; ++h1)
+                for (int h2 = 0; h2 < gm.nH[1]; ++h2)
+                    for (int h3 = 0; h3 < gm.nH[2]; ++h3) {
+                        const int hh[3] = {h1, h2, h3};
+                        int lo[3], hi[3];
+                        for (int a = 0; a < 3; ++a) {
+                            const int H = gm.Hmin[a] + hh[a];
+                            lo[a] = std::max(g.n[a] * H, gm.g0[a]);
+                            hi[a] = std::min(g.n[a] * (H + 1) - 1, gm.g0[a] + gm.cnt[a] - 1);
+                        }
+                        double qmax = 0.0;
+                        for (int c = 0; c < 8; ++c) {
+                            const double Gc[3] = {(double)((c & 4) ? hi[0] : lo[0]) / g.n[0],
+                                                  (double)((c & 2) ? hi[1] : lo[1]) / g.n[1],
+                                                  (double)((c & 1) ? hi[2] : lo[2]) / g.n[2]};
+                            double Qc[3];
+                            for (int a = 0; a < 3; ++a)
+                                Qc[a] = Gc[0] * M->recip[a] + Gc[1] * M->recip[3 + a] + Gc[2] * M->recip[6 + a];
+                            qmax = std::max(qmax, sqrt(Qc[0] * Qc[0] + Qc[1] * Qc[1] + Qc[2] * Qc[2]));
+                        }
+                        const double xz = std::min(qmax * umax, xmax);
+                        pz[((size_t)h1 * gm.nH[1] + h2) * gm.nH[2] + h3] = std::min(P, taylor_order_for(xz, o->taylor_eps));
+                    }
+            int *d_pz = (int *)ws.get(sizeof(int) * nz);
+            int *tab = nullptr;
+            if (ws.failed) return ds_fail(ctx, DS_ERR_OOM, "device allocation failed (zone orders)");
+            rc = sub_simplex_tables(M, P, &tab);
+            if (rc != DS_OK) return rc;
+            CK(cudaMemcpyAsync(d_pz, pz.data(), sizeof(int) * nz, cudaMemcpyHostToDevice, st));
+            const size_t nsub = (size_t)(P + 1) * (P + 2) * (P + 3) * (P + 4) / 24;
+            p.pzone = d_pz;
+            p.sub_map = tab;
+            p.sub_ops = tab + nsub;
+            p.sub_off = tab + 2 * nsub;
+        }
         if (keep) {
             keep->terms = d_terms;
             keep->pw = pw;
@@ -818,7 +996,7 @@ ds_status plan_and_run(ds_model *M, const ds_qgrid *q, const ds_opts *o, T *d_ou
 // the request's kernels on stream st into the device volume d_out (no synchronisation)
 template <typename T>
 ds_status enqueue_request(ds_model *M, const ds_qgrid *q, const ds_opts *o, T *d_out, cudaStream_t st, Scratch &ws,
-                          ds_result_info *info) {
+                          ds_result_info *info, const TaylorHint *hint) {
     ds_ctx *ctx = M->ctx;
     int g0[3], cnt[3];
     ds_status rc = grid_indices(ctx, M, q, g0, cnt);
@@ -832,13 +1010,13 @@ ds_status enqueue_request(ds_model *M, const ds_qgrid *q, const ds_opts *o, T *d
         T *t1 = (T *)ws.get(sizeof(T) * next);
         T *t2 = (T *)ws.get(sizeof(T) * next);
         if (ws.failed) return ds_fail(ctx, DS_ERR_OOM, "device allocation failed (Lanczos buffers)");
-        rc = plan_and_run<T>(M, q, o, ext, st, ws, info, nullptr);
+        rc = plan_and_run<T>(M, q, o, ext, st, ws, info, nullptr, hint);
         if (rc == DS_OK) {
             ProfScope ps(ctx, "lanczos", st);
             lanczos_resample<T>(ext, t1, t2, d_out, cnt, o->lanczos_m, o->lanczos_mprime, st);
         }
     } else {
-        rc = plan_and_run<T>(M, q, o, d_out, st, ws, info, nullptr);
+        rc = plan_and_run<T>(M, q, o, d_out, st, ws, info, nullptr, hint);
     }
     if (rc == DS_OK && info) {
         info->nvox = (int64_t)cnt[0] * cnt[1] * cnt[2];
@@ -901,9 +1079,9 @@ extern "C" ds_status ds_request_intensity(ds_model *M, const ds_qgrid *q, const 
 }
 
 template ds_status plan_and_run<float>(ds_model *, const ds_qgrid *, const ds_opts *, float *, cudaStream_t,
-                                       Scratch &, ds_result_info *, ForwardKeep<float> *);
+                                       Scratch &, ds_result_info *, ForwardKeep<float> *, const TaylorHint *);
 template ds_status plan_and_run<double>(ds_model *, const ds_qgrid *, const ds_opts *, double *, cudaStream_t,
-                                        Scratch &, ds_result_info *, ForwardKeep<double> *);
+                                        Scratch &, ds_result_info *, ForwardKeep<double> *, const TaylorHint *);
 
 // ------------------------------------------------------------------------------------------
 // tracing
@@ -994,6 +1172,6 @@ extern "C" ds_status ds_profile_report(ds_ctx *ctx, char *json, size_t cap) {
 }
 
 template ds_status enqueue_request<float>(ds_model *, const ds_qgrid *, const ds_opts *, float *, cudaStream_t,
-                                          Scratch &, ds_result_info *);
+                                          Scratch &, ds_result_info *, const TaylorHint *);
 template ds_status enqueue_request<double>(ds_model *, const ds_qgrid *, const ds_opts *, double *, cudaStream_t,
-                                           Scratch &, ds_result_info *);
+                                           Scratch &, ds_result_info *, const TaylorHint *);

@@ -41,12 +41,25 @@ struct ds_model {
     ds::FormFactors<float> ff32;
     ds::FormFactors<double> ff64;
     ds::SiteGroups groups;
+    int period[3] = {0, 0, 0};            // smallest d <= 64 with d r_mu,a integral for all sites (0: none)
+    // per-site means of the uploaded data (Eq. occ: c_mu; mean moments), computed at upload
+    double *d_mean_occ = nullptr;         // [site]
+    double *d_mean_spin = nullptr;        // [site][3]
+    cudaEvent_t ready = nullptr;          // recorded after every upload; every request stream waits on it
+    // site phase tables per grid, built by the first request that needs them
+    struct SiteTables {
+        void *phk = nullptr, *phH = nullptr;
+        cudaEvent_t done = nullptr;       // recorded after the tables' kernel on the building stream
+    };
+    std::map<std::vector<int>, SiteTables> site_tables;  // (precision, Hmin, nH) -> tables
+    std::mutex cache_mu;                  // guards the caches of this model (serving worker and callers)
     int *d_site_of = nullptr;
     float *d_scat32 = nullptr;
     double *d_scat64 = nullptr;
     ds::c_t<float> *d_tw32[3] = {nullptr, nullptr, nullptr};
     ds::c_t<double> *d_tw64[3] = {nullptr, nullptr, nullptr};
     std::map<int, std::pair<int4 *, int *>> taylor_tables;   // order P -> (terms, ops) on device
+    std::map<int, int *> sub_tables;                          // order P -> sub-simplex tables (map, ops, off)
 };
 
 struct ProfRecord {
@@ -124,16 +137,22 @@ void monomial_tables(int P, std::vector<int4> &terms, std::vector<int> &ops);
 int taylor_order_for(double xmax, double eps);
 void box_corners(const ds_model *M, const int g0[3], const int cnt[3], double corners[24]);
 
+// a Taylor order resolved ahead of launch (serving plans on the submitting thread)
+struct TaylorHint {
+    int P;
+    double xmax, umax;
+};
+
 // the forward calculation into a device buffer on stream st, scratch from ws
 template <typename T>
 ds_status plan_and_run(ds_model *M, const ds_qgrid *q, const ds_opts *o, T *d_out, cudaStream_t st, Scratch &ws,
-                       ds_result_info *info, ForwardKeep<T> *keep);
+                       ds_result_info *info, ForwardKeep<T> *keep, const TaylorHint *hint = nullptr);
 // all kernels of one request into a device volume, no synchronisation (smoothing included)
 template <typename T>
 ds_status enqueue_request(ds_model *M, const ds_qgrid *q, const ds_opts *o, T *d_out, cudaStream_t st, Scratch &ws,
-                          ds_result_info *info);
+                          ds_result_info *info, const TaylorHint *hint = nullptr);
 ds_status resolve_taylor_order(ds_model *M, const ds_qgrid *q, const ds_opts *o, cudaStream_t st, Scratch &ws, int *P,
-                               double *xmax);
+                               double *xmax, double *umax = nullptr);
 size_t request_footprint(const ds_model *M, const ds_qgrid *q, const ds_opts *o, int P);
 // sub-box averaging (subbox.cu)
 template <typename T>

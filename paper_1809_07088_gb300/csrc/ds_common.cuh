@@ -87,6 +87,13 @@ constexpr double FOUR_PI_D = 12.566370614359172953850573533118;
 // (a few ulp, far inside the FP32 path's error budget)
 __device__ __forceinline__ double exp_w(double x) { return exp(x); }
 __device__ __forceinline__ float exp_w(float x) { return __expf(x); }
+// 2^x: the SFU's approximate base-2 exponential (PTX ex2.approx) in FP32, exp2 in FP64
+__device__ __forceinline__ double exp2_w(double x) { return exp2(x); }
+__device__ __forceinline__ float exp2_w(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
 __device__ __forceinline__ double div_w(double a, double b) { return a / b; }
 __device__ __forceinline__ float div_w(float a, float b) { return __fdividef(a, b); }
 

@@ -175,8 +175,11 @@ void fft_real_fields(const Geometry &g, const FieldSource &src, int f0, int nf, 
                      const c_t<T> *W1, const c_t<T> *W2, const c_t<T> *W3, cudaStream_t s) {
     using C = c_t<T>;
     const size_t ce = sizeof(C);
-    // pass 1
-    const int ppc = plane_batch(g, ce, 48 * 1024);
+    // pass 1: planes per CTA bounded by 48 KB of shared memory, and small enough that the
+    // grid gives a few waves over the 152 SMs even for a small batch of fields
+    const int target_ctas = 152 * 4;
+    int ppc = plane_batch(g, ce, 48 * 1024);
+    ppc = std::max(1, std::min(ppc, (int)(((size_t)g.n[0] * nf + target_ctas - 1) / target_ctas)));
     const int n2p = (g.n[1] + 1) / 2;
     const size_t plane_c = (size_t)std::max(n2p * g.n[2], g.n[1] * g.n3h);
     size_t sm1 = (g.n[1] + g.n[2] + 2 * ppc * plane_c) * ce;
@@ -187,6 +190,9 @@ void fft_real_fields(const Geometry &g, const FieldSource &src, int f0, int nf, 
     const int ncol = g.n[1] * g.n3h;
     int cb = (int)((48 * 1024 / ce - g.n[0]) / (2 * g.n[0]));
     cb = std::max(1, std::min(cb, ncol));
+    // columns per CTA: at least 32 (coalesced rows), fewer when the batch is small
+    const int cb_small = (int)(((size_t)ncol * nf + target_ctas - 1) / target_ctas);
+    cb = std::max(std::min(cb, 32), std::min(cb, cb_small));
     size_t sm2 = (g.n[0] + 2 * (size_t)g.n[0] * cb) * ce;
     dim3 g2((unsigned)(((ncol + cb - 1) / cb) * (size_t)nf));
     k_fft_columns<T><<<g2, 256, sm2, s>>>(g, src, f0, cb, work, spec, W1);

@@ -62,7 +62,33 @@ template <typename T> struct FormFactors {
     int cls_end[MAX_FF_CLASSES];    // exclusive end (sorted position)
     int cls_kind[MAX_FF_CLASSES];
     T cls_coef[MAX_FF_CLASSES][9];
+    // the same form factors as sums of Gaussians in |Q|^2: f = gc + sum_{i < ng} ga_i 2^(gb_i |Q|^2)
+    int cls_ng[MAX_FF_CLASSES];
+    T cls_ga[MAX_FF_CLASSES][4], cls_gb[MAX_FF_CLASSES][4], cls_gc[MAX_FF_CLASSES];
 };
+
+// fills the Gaussian-sum form of class c from its kind and coefficients (s = |Q| / 4 pi)
+template <typename T> inline void gaussian_sum_form(FormFactors<T> &ff, int c, int kind, const double *coef) {
+    const double to_q2 = 1.4426950408889634 / (16.0 * 9.869604401089358);  // log2(e) / (4 pi)^2
+    double a[4] = {0, 0, 0, 0}, b[4] = {0, 0, 0, 0}, c0 = 1.0;
+    int ng = 0;
+    if (kind == 1) {  // sum_i a_i exp(-b_i s^2) + c
+        for (int i = 0; i < 4; ++i) a[i] = coef[i], b[i] = coef[4 + i];
+        ng = 4;
+        c0 = coef[8];
+    } else if (kind == 2) {  // A exp(-a s^2) + B exp(-b s^2) + C exp(-c s^2) + D
+        a[0] = coef[0], b[0] = coef[1], a[1] = coef[2], b[1] = coef[3];
+        ng = 2;
+        if (coef[4] != 0.0) a[2] = coef[4], b[2] = coef[5], ng = 3;
+        c0 = coef[6];
+    }
+    ff.cls_ng[c] = ng;
+    for (int i = 0; i < 4; ++i) {
+        ff.cls_ga[c][i] = (T)a[i];
+        ff.cls_gb[c][i] = (T)(-b[i] * to_q2);
+    }
+    ff.cls_gc[c] = (T)c0;
+}
 
 // sites sorted by (form-factor class, z = r_mu,3 mod 1); a group = sites of one class sharing z,
 // so that exp(2 pi i H3 z) is common to the group
@@ -91,16 +117,30 @@ template <typename T> struct RecombParams {
     FormFactors<T> ff;
     SiteGroups grp;
     double recip[9];                    // a*, b*, c* rows (1/A)
+    T qstep[9];                         // a*/n1, b*/n2, c*/n3 rows: Q = sum_a G_a qstep_a
     double qscale;                      // displacive: coefficient uses Q / qscale
     T norm;                             // 1/(nmodels N), times C for magnetic
     const int *ops;                     // displacive coefficient update codes per monomial
     const int4 *terms;                  // displacive monomials (a, b, c, n)
+    const int *pzone;                   // optional: Taylor order of each zone [nH1][nH2][nH3]
+    const int *sub_map;                 // order-p sub-simplex in lexicographic order -> global monomial
+    const int *sub_ops;                 // its coefficient update codes
+    const int *sub_off;                 // offset of order p in sub_map / sub_ops
     const c_t<T> *bragg;                // displacive DIFFUSE: <F(H)> per zone [nH1][nH2][nH3]
     T *out;                             // [cnt1][cnt2][cnt3]
     c_t<T> *Fout;                       // optional: F per voxel [model][voxel][ncomp] (adjoint)
     int force_plain;                    // use the per-site (ungrouped) recombination
+    int dres[3];                        // residue classes of zones per axis (0: per-zone kernels)
     int *err;
 };
+
+// reciprocal rows (FP64, Cartesian 1/A) and their per-supercell-index steps in the working type
+template <typename T> inline void set_reciprocal(RecombParams<T> &p, const double recip[9], const int n[3]) {
+    for (int i = 0; i < 9; ++i) {
+        p.recip[i] = recip[i];
+        p.qstep[i] = (T)(recip[i] / n[i / 3]);
+    }
+}
 
 // ---- launchers (fft.cu) --------------------------------------------------------------------
 template <typename T> void make_twiddles(int n, c_t<T> *W, cudaStream_t s);
@@ -121,8 +161,11 @@ void site_means_spin(int nmodels, int nsite, int ncell, const float *spins, doub
 struct Corners {
     double v[24];  // 8 Cartesian Q vectors
 };
-void corner_xmax(int natom, const float *disp, const Corners &corners, double *out /*dev [8]*/, cudaStream_t s);
+// out (device, 9 doubles): max_j |Q_c . u_j| for the 8 corners, then max_j |u_j|
+void corner_xmax(int natom, const float *disp, const Corners &corners, double *out, cudaStream_t s);
 template <typename T> void recombine_cm(const RecombParams<T> &p, cudaStream_t s);
+// recomb_res.cu: the residue-class kernel when p.dres is set; false when it does not apply
+template <typename T> bool recombine_cm_residues(const RecombParams<T> &p, cudaStream_t s);
 template <typename T> void recombine_disp(const RecombParams<T> &p, cudaStream_t s);
 template <typename T>
 void displacive_bragg(const RecombParams<T> &p, const int4 *terms, c_t<T> *avg0, c_t<T> *bragg, cudaStream_t s);

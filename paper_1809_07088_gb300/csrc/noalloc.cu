@@ -118,6 +118,7 @@ extern "C" ds_status ds_occupancy_intensity_noalloc(const double lattice[6], int
     for (int c = 1; c < MAX_FF_CLASSES; ++c) G.cls_grp_end[c] = -1;
     p.ff.ncls = 1;
     p.ff.cls_kind[0] = DS_FF_CONST;
+    gaussian_sum_form(p.ff, 0, DS_FF_CONST, nullptr);
     p.ff.cls_end[0] = nsite;
     for (int c = 1; c < MAX_FF_CLASSES; ++c) p.ff.cls_end[c] = -1;
 
@@ -177,7 +178,7 @@ extern "C" ds_status ds_occupancy_intensity_noalloc(const double lattice[6], int
     p.nmodels = nmodels;
     p.ncomp = 1;
     p.diffuse = mode == DS_DIFFUSE;
-    memcpy(p.recip, B, sizeof(B));
+    set_reciprocal(p, B, g.n);
     p.norm = (float)(1.0 / ((double)nmodels * nsite * g.ncell));
     p.nmax = nmax;
     p.nHmax = nHmax;

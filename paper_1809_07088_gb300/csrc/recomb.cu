@@ -126,19 +126,21 @@ void site_means_spin(int nmodels, int nsite, int ncell, const float *spins, doub
 
 // out[c] = max_j |Q_c . u_j| for the 8 corners of the Q box (non-negative doubles order like
 // their bit patterns, so an integer atomicMax is exact)
+// out[8] = max_j |u_j| as well
 __global__ void k_corner_xmax(int natom, const float *disp, const Corners cq, unsigned long long *out) {
     const double *corners = cq.v;
-    double best[8];
+    double best[9];
 #pragma unroll
-    for (int c = 0; c < 8; ++c) best[c] = 0.0;
+    for (int c = 0; c < 9; ++c) best[c] = 0.0;
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < natom; j += gridDim.x * blockDim.x) {
         const double ux = disp[3 * (size_t)j], uy = disp[3 * (size_t)j + 1], uz = disp[3 * (size_t)j + 2];
 #pragma unroll
         for (int c = 0; c < 8; ++c)
             best[c] = fmax(best[c], fabs(corners[3 * c] * ux + corners[3 * c + 1] * uy + corners[3 * c + 2] * uz));
+        best[8] = fmax(best[8], sqrt(ux * ux + uy * uy + uz * uz));
     }
 #pragma unroll
-    for (int c = 0; c < 8; ++c) {
+    for (int c = 0; c < 9; ++c) {
         double v = best[c];
         for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
         if ((threadIdx.x & 31) == 0) atomicMax(out + c, (unsigned long long)__double_as_longlong(v));
@@ -146,7 +148,7 @@ __global__ void k_corner_xmax(int natom, const float *disp, const Corners cq, un
 }
 
 void corner_xmax(int natom, const float *disp, const Corners &corners, double *out, cudaStream_t s) {
-    cudaMemsetAsync(out, 0, 8 * sizeof(double), s);
+    cudaMemsetAsync(out, 0, 9 * sizeof(double), s);
     int nb = std::min(1024, std::max(1, (natom + 255) / 256));
     k_corner_xmax<<<nb, 256, 0, s>>>(natom, disp, corners, (unsigned long long *)out);
     count_launches(1);
@@ -266,8 +268,8 @@ __global__ void __launch_bounds__(256, MINB)
         T Q12[3], c3[3];
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            Q12[a] = (T)((double)G1 / g.n[0] * p.recip[a] + (double)G2 / g.n[1] * p.recip[3 + a]);
-            c3[a] = (T)(p.recip[6 + a] / g.n[2]);
+            Q12[a] = fma((T)G1, p.qstep[a], (T)G2 * p.qstep[3 + a]);
+            c3[a] = p.qstep[6 + a];
         }
         for (int h3 = h3lo; h3 <= h3hi; h3 += VPI) {
             C F[VPI][NC], part[VPI][NC];
@@ -498,8 +500,8 @@ __global__ void __launch_bounds__(256, MINB)
         T Q12[3], c3[3];
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            Q12[a] = (T)((double)G1 / g.n[0] * p.recip[a] + (double)G2 / g.n[1] * p.recip[3 + a]);
-            c3[a] = (T)(p.recip[6 + a] / g.n[2]);
+            Q12[a] = fma((T)G1, p.qstep[a], (T)G2 * p.qstep[3 + a]);
+            c3[a] = p.qstep[6 + a];
         }
         // exp(2 pi i H3 z_g) of the first voxel, then advanced by exp(2 pi i z_g) per zone step
         C wcur[MAXG], wstep[MAXG];
@@ -637,6 +639,7 @@ template <typename T, int NC, int MAXS> static void launch_cm(const RecombParams
 }
 
 template <typename T> void recombine_cm(const RecombParams<T> &p, cudaStream_t s) {
+    if (recombine_cm_residues<T>(p, s)) return;
     if (p.ncomp == 1) {
         if (p.nsite <= 4) launch_cm<T, 1, 4>(p, s);
         else if (p.nsite <= 8) launch_cm<T, 1, 8>(p, s);
@@ -653,14 +656,26 @@ template <typename T> void recombine_cm(const RecombParams<T> &p, cudaStream_t s
 // displacive (Taylor) recombination
 // ------------------------------------------------------------------------------------------
 // CTA: KT consecutive k (one warp each) x a chunk of 32*ZPT zones of each k's own zone box.
-// The transforms M_mu,t(k) of a chunk of TC monomials are staged in shared memory and read by
-// all lanes of a warp at once; each lane keeps the scaled coefficients
+// The transforms M_mu,t(k) of the CTA's k are staged TC monomials at a time in shared memory
+// by asynchronous copies, double buffered (the next chunk is in flight while the current one is
+// used), and read by all lanes of a warp at once.  Each lane keeps the scaled coefficients
 // (Qx/Qs)^a (Qy/Qs)^b (Qz/Qs)^c of its ZPT voxels, updated with one multiply per monomial
 // (monomials run in lexicographic (a, b, c) order), and accumulates S_mu += coef * M_mu,t.
+// A k of the other half of the spectrum reads the stored i^n M(-k): its value is
+// (-1)^n conj(stored), applied with compile-time signs in a separate loop body.
 
-constexpr int DISP_KT = 4;
+constexpr int DISP_KT = 8;
 constexpr int DISP_TC = 32;
 enum { OP_MULZ = 0, OP_NEWB = 1, OP_NEWA = 2, OP_INIT = 3 };
+
+template <int BYTES> __device__ __forceinline__ void cp_async(void *smem, const void *gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(s), "l"(gmem), "n"(BYTES) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N> __device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
 
 struct ZoneBox {
     int lo[3], n[3];
@@ -679,23 +694,108 @@ __device__ __forceinline__ ZoneBox zone_box(const Geometry &g, const GridMap &gm
     return b;
 }
 
+// one chunk of monomials for one warp; CONJ: the warp's k reads the mirrored half spectrum;
+// MASK: a voxel takes only the monomials of order n <= its zone's order pzv[j]
+template <typename T, int MAXS, int ZPT, bool CONJ, bool MASK>
+__device__ __forceinline__ void disp_chunk(const c_t<T> *wt, const int *tinfo, int tc, int nsite, const T (&qx)[ZPT],
+                                           const T (&qy)[ZPT], const T (&qz)[ZPT], const int (&pzv)[ZPT],
+                                           T (&ca)[ZPT], T (&cb)[ZPT], T (&cc)[ZPT], c_t<T> (&S)[ZPT][MAXS]) {
+    for (int tt = 0; tt < tc; ++tt) {
+        const int info = tinfo[tt];
+        const int op = info & 3;
+        const int n = info >> 2;
+        T w[ZPT];
+#pragma unroll
+        for (int j = 0; j < ZPT; ++j) {
+            if (op == OP_MULZ) {
+                cc[j] *= qz[j];
+            } else if (op == OP_NEWB) {
+                cb[j] *= qy[j];
+                cc[j] = cb[j];
+            } else if (op == OP_NEWA) {
+                ca[j] *= qx[j];
+                cb[j] = ca[j];
+                cc[j] = ca[j];
+            } else {
+                ca[j] = cb[j] = cc[j] = T(1);
+            }
+            w[j] = (!MASK || n <= pzv[j]) ? cc[j] : T(0);
+        }
+        if (!CONJ) {
+#pragma unroll
+            for (int s = 0; s < MAXS; ++s) {
+                if (s < nsite) {
+                    const c_t<T> m = wt[(size_t)s * DISP_TC + tt];
+#pragma unroll
+                    for (int j = 0; j < ZPT; ++j) {
+                        S[j][s].x = fma(w[j], m.x, S[j][s].x);
+                        S[j][s].y = fma(w[j], m.y, S[j][s].y);
+                    }
+                }
+            }
+        } else if (n & 1) {  // odd order: value (-x, +y)
+#pragma unroll
+            for (int s = 0; s < MAXS; ++s) {
+                if (s < nsite) {
+                    const c_t<T> m = wt[(size_t)s * DISP_TC + tt];
+#pragma unroll
+                    for (int j = 0; j < ZPT; ++j) {
+                        S[j][s].x = fma(-w[j], m.x, S[j][s].x);
+                        S[j][s].y = fma(w[j], m.y, S[j][s].y);
+                    }
+                }
+            }
+        } else {  // even order: value (+x, -y)
+#pragma unroll
+            for (int s = 0; s < MAXS; ++s) {
+                if (s < nsite) {
+                    const c_t<T> m = wt[(size_t)s * DISP_TC + tt];
+#pragma unroll
+                    for (int j = 0; j < ZPT; ++j) {
+                        S[j][s].x = fma(w[j], m.x, S[j][s].x);
+                        S[j][s].y = fma(-w[j], m.y, S[j][s].y);
+                    }
+                }
+            }
+        }
+    }
+}
+
 template <typename T, int MAXS, int ZPT>
-__global__ void __launch_bounds__(DISP_KT * 32) k_recomb_disp(RecombParams<T> p) {
+__global__ void __launch_bounds__(DISP_KT * 32) k_recomb_disp(const __grid_constant__ RecombParams<T> p) {
     using C = c_t<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ int kidx_s[DISP_KT], kconj_s[DISP_KT], site_s[MAXS];
     const Geometry &g = p.g;
     const GridMap &gm = p.gm;
     const int nsite = p.nsite, nT = p.nT;
-    C *tile = (C *)smem_raw;                                      // [KT][nsite][TC]
-    int *ops_s = (int *)(tile + (size_t)DISP_KT * nsite * DISP_TC);
+    const size_t stage_elems = (size_t)DISP_KT * nsite * DISP_TC;
+    C *tile = (C *)smem_raw;                                   // [2][KT][nsite][TC]
+    int *tinfo = (int *)(tile + 2 * stage_elems);              // [2][TC]: op | n << 2
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int k = blockIdx.x * DISP_KT + warp;
+    const int k0 = blockIdx.x * DISP_KT;
+    const int k = k0 + warp;
+    if (threadIdx.x < DISP_KT) {
+        const int kf = k0 + threadIdx.x;
+        int cj = 0, ki = -1;
+        if (kf < g.ncell) {
+            const int f3 = kf % g.n[2], f2 = (kf / g.n[2]) % g.n[1], f1 = kf / (g.n[2] * g.n[1]);
+            ki = half_index(g, f1, f2, f3, cj);
+        }
+        kidx_s[threadIdx.x] = ki;
+        kconj_s[threadIdx.x] = cj;
+    }
+    if (threadIdx.x < MAXS && threadIdx.x < nsite) site_s[threadIdx.x] = p.site_of[threadIdx.x];
+    __syncthreads();
+
     const bool kvalid = k < g.ncell;
     const int kq = kvalid ? k : 0;
     const int k3 = kq % g.n[2], k2 = (kq / g.n[2]) % g.n[1], k1 = kq / (g.n[2] * g.n[1]);
     const ZoneBox zb = zone_box(g, gm, k1, k2, k3);
     const int nzk = kvalid ? zb.n[0] * zb.n[1] * zb.n[2] : 0;
     const int zbase = blockIdx.y * (32 * ZPT);
+    const bool active = zbase < nzk;  // warp-uniform
+    const bool conj = kconj_s[warp] != 0;
 
     T qx[ZPT], qy[ZPT], qz[ZPT], ca[ZPT], cb[ZPT], cc[ZPT];
     int Gz[ZPT][3];
@@ -722,63 +822,86 @@ __global__ void __launch_bounds__(DISP_KT * 32) k_recomb_disp(RecombParams<T> p)
 #pragma unroll
         for (int s = 0; s < MAXS; ++s) S[j][s] = mk<T>(T(0), T(0));
 
-    const bool active = zbase < nzk;  // warp-uniform
-    for (int t0 = 0; t0 < nT; t0 += DISP_TC) {
-        const int tc = min(DISP_TC, nT - t0);
+    // Taylor order of this CTA: the largest zone order among its voxels (all orders when no
+    // per-zone table is given); its monomials are the order-Pc sub-simplex in lexicographic order
+    __shared__ int pcta_s;
+    int nTc = nT;
+    int pzv[ZPT];
+#pragma unroll
+    for (int j = 0; j < ZPT; ++j) pzv[j] = 0;
+    const int *tmap = nullptr, *tops = p.ops;
+    if (p.pzone) {
+        if (threadIdx.x == 0) pcta_s = 0;
         __syncthreads();
-        for (int idx = threadIdx.x; idx < DISP_KT * nsite * tc; idx += blockDim.x) {
+        int pm = 0;
+#pragma unroll
+        for (int j = 0; j < ZPT; ++j) {
+            pzv[j] = 0;
+            if (zbase + lane + 32 * j < nzk) {
+                const int h1 = (Gz[j][0] - k1) / g.n[0] - gm.Hmin[0];
+                const int h2 = (Gz[j][1] - k2) / g.n[1] - gm.Hmin[1];
+                const int h3 = (Gz[j][2] - k3) / g.n[2] - gm.Hmin[2];
+                pzv[j] = p.pzone[((size_t)h1 * gm.nH[1] + h2) * gm.nH[2] + h3];
+                pm = max(pm, pzv[j]);
+            }
+        }
+        for (int o = 16; o > 0; o >>= 1) pm = max(pm, __shfl_xor_sync(0xffffffffu, pm, o));
+        if (lane == 0) atomicMax(&pcta_s, pm);
+        __syncthreads();
+        const int Pc = pcta_s;
+        nTc = (Pc + 1) * (Pc + 2) * (Pc + 3) / 6;
+        tmap = p.sub_map + p.sub_off[Pc];
+        tops = p.sub_ops + p.sub_off[Pc];
+    }
+
+    auto load_chunk = [&](int stage, int t0) {
+        const int tc = min(DISP_TC, nTc - t0);
+        C *dst = tile + stage * stage_elems;
+        for (int idx = threadIdx.x; idx < DISP_KT * nsite * DISP_TC; idx += blockDim.x) {
             const int kk = idx % DISP_KT;
             const int rest = idx / DISP_KT;
-            const int tt = rest % tc, s = rest / tc;
-            const int kf = blockIdx.x * DISP_KT + kk;
-            C v = mk<T>(T(0), T(0));
-            if (kf < g.ncell) {
-                const int f3 = kf % g.n[2], f2 = (kf / g.n[2]) % g.n[1], f1 = kf / (g.n[2] * g.n[1]);
-                int cj;
-                const int ki = half_index(g, f1, f2, f3, cj);
-                const int site = p.site_of[s];
-                v = p.spec[(((size_t)p.model * nsite + site) * nT + t0 + tt) * g.ncell_h + ki];
-                // stored: i^n M(k) on the half spectrum; i^n M(k) = (-1)^n conj(i^n M(-k))
-                if (cj) {
-                    v = cconj(v);
-                    if (p.terms[t0 + tt].w & 1) v = mk<T>(-v.x, -v.y);
-                }
+            const int tt = rest % DISP_TC, s = rest / DISP_TC;
+            C *d = dst + ((size_t)kk * nsite + s) * DISP_TC + tt;
+            const int ki = kidx_s[kk];
+            if (tt < tc && ki >= 0) {
+                const int t = tmap ? tmap[t0 + tt] : t0 + tt;
+                cp_async<sizeof(C)>(d, p.spec + (((size_t)p.model * nsite + site_s[s]) * nT + t) * g.ncell_h + ki);
+            } else {
+                *d = mk<T>(T(0), T(0));
             }
-            tile[((size_t)kk * nsite + s) * DISP_TC + tt] = v;
         }
-        for (int tt = threadIdx.x; tt < tc; tt += blockDim.x) ops_s[tt] = p.ops[t0 + tt];
+        for (int tt = threadIdx.x; tt < DISP_TC; tt += blockDim.x) {
+            int info = 0;
+            if (tt < tc) {
+                const int t = tmap ? tmap[t0 + tt] : t0 + tt;
+                info = tops[t0 + tt] | (p.terms[t].w << 2);
+            }
+            tinfo[stage * DISP_TC + tt] = info;
+        }
+        cp_async_commit();
+    };
+
+    const int nchunk = (nTc + DISP_TC - 1) / DISP_TC;
+    load_chunk(0, 0);
+    for (int c = 0; c < nchunk; ++c) {
+        if (c + 1 < nchunk) load_chunk((c + 1) & 1, (c + 1) * DISP_TC);
+        else cp_async_commit();
+        cp_async_wait<1>();
         __syncthreads();
-        if (!active) continue;
-        const C *wt = tile + (size_t)warp * nsite * DISP_TC;
-        for (int tt = 0; tt < tc; ++tt) {
-            const int op = ops_s[tt];
-#pragma unroll
-            for (int j = 0; j < ZPT; ++j) {
-                if (op == OP_MULZ) {
-                    cc[j] *= qz[j];
-                } else if (op == OP_NEWB) {
-                    cb[j] *= qy[j];
-                    cc[j] = cb[j];
-                } else if (op == OP_NEWA) {
-                    ca[j] *= qx[j];
-                    cb[j] = ca[j];
-                    cc[j] = ca[j];
-                } else {
-                    ca[j] = cb[j] = cc[j] = T(1);
-                }
-            }
-#pragma unroll
-            for (int s = 0; s < MAXS; ++s) {
-                if (s < nsite) {
-                    const C m = wt[(size_t)s * DISP_TC + tt];
-#pragma unroll
-                    for (int j = 0; j < ZPT; ++j) {
-                        S[j][s].x = fma(cc[j], m.x, S[j][s].x);
-                        S[j][s].y = fma(cc[j], m.y, S[j][s].y);
-                    }
-                }
+        if (active) {
+            const int stage = c & 1;
+            const int tc = min(DISP_TC, nTc - c * DISP_TC);
+            const C *wt = tile + stage * stage_elems + (size_t)warp * nsite * DISP_TC;
+            const int *ti = tinfo + stage * DISP_TC;
+            if (p.pzone) {
+                if (conj) disp_chunk<T, MAXS, ZPT, true, true>(wt, ti, tc, nsite, qx, qy, qz, pzv, ca, cb, cc, S);
+                else disp_chunk<T, MAXS, ZPT, false, true>(wt, ti, tc, nsite, qx, qy, qz, pzv, ca, cb, cc, S);
+            } else {
+                if (conj) disp_chunk<T, MAXS, ZPT, true, false>(wt, ti, tc, nsite, qx, qy, qz, pzv, ca, cb, cc, S);
+                else disp_chunk<T, MAXS, ZPT, false, false>(wt, ti, tc, nsite, qx, qy, qz, pzv, ca, cb, cc, S);
             }
         }
+        __syncthreads();
     }
     if (!active) return;
 
@@ -797,7 +920,7 @@ __global__ void __launch_bounds__(DISP_KT * 32) k_recomb_disp(RecombParams<T> p)
 #pragma unroll
         for (int s = 0; s < MAXS; ++s) {
             if (s < nsite) {
-                const int site = p.site_of[s];
+                const int site = site_s[s];
                 const C *tH = p.phH + (size_t)site * 3 * p.nHmax;
                 const C *tk = p.phk + (size_t)site * 3 * p.nmax;
                 C ph = cmul(cmul(tH[h1], tH[p.nHmax + h2]), tH[2 * p.nHmax + h3]);
@@ -831,7 +954,7 @@ template <typename T, int MAXS, int ZPT> static void launch_disp(const RecombPar
     int nzmax = 1;
     for (int a = 0; a < 3; ++a) nzmax *= (p.gm.cnt[a] + p.g.n[a] - 1) / p.g.n[a] + 1;
     dim3 grid((p.g.ncell + DISP_KT - 1) / DISP_KT, (nzmax + 32 * ZPT - 1) / (32 * ZPT));
-    const size_t sm = (size_t)DISP_KT * p.nsite * DISP_TC * sizeof(C) + DISP_TC * sizeof(int);
+    const size_t sm = 2 * (size_t)DISP_KT * p.nsite * DISP_TC * sizeof(C) + 2 * DISP_TC * sizeof(int);
     if (sm > 48 * 1024)
         cudaFuncSetAttribute(k_recomb_disp<T, MAXS, ZPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     k_recomb_disp<T, MAXS, ZPT><<<grid, DISP_KT * 32, sm, s>>>(p);
@@ -840,7 +963,7 @@ template <typename T, int MAXS, int ZPT> static void launch_disp(const RecombPar
 
 template <typename T> void recombine_disp(const RecombParams<T> &p, cudaStream_t s) {
     constexpr bool dbl = sizeof(T) == 8;
-    if (p.nsite <= 4) launch_disp<T, 4, dbl ? 4 : 8>(p, s);
+    if (p.nsite <= 4) launch_disp<T, 4, dbl ? 2 : 4>(p, s);
     else if (p.nsite <= 8) launch_disp<T, 8, dbl ? 2 : 4>(p, s);
     else launch_disp<T, 16, dbl ? 1 : 2>(p, s);
 }
@@ -874,6 +997,7 @@ __global__ void k_bragg_disp(RecombParams<T> p, const c_t<T> *avg0, c_t<T> *brag
     const T s2 = q2 * (T)(1.0 / (FOUR_PI_D * FOUR_PI_D));
     C F = mk<T>(T(0), T(0)), part = mk<T>(T(0), T(0));
     int cls = 0;
+    const int pz = p.pzone ? p.pzone[z] : 1 << 30;  // the zone's Taylor order
     for (int s = 0; s < p.nsite; ++s) {
         const int site = p.site_of[s];
         double ca = 1, cb = 1, cc = 1;
@@ -884,6 +1008,7 @@ __global__ void k_bragg_disp(RecombParams<T> p, const c_t<T> *avg0, c_t<T> *brag
             else if (op == OP_NEWB) { cb *= qy; cc = cb; }
             else if (op == OP_NEWA) { ca *= qx; cb = ca; cc = ca; }
             else { ca = cb = cc = 1; }
+            if (p.terms[t].w > pz) continue;
             const C m = avg0[(size_t)site * p.nT + t];
             S.x += (T)cc * m.x;
             S.y += (T)cc * m.y;

@@ -37,6 +37,8 @@ struct ServeJob {
     void *out = nullptr;
     size_t footprint = 0;
     double xmax = -1.0;
+    bool has_hint = false;
+    TaylorHint hint;
     cudaStream_t stream = nullptr;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     double t_submit = 0.0, t_done = 0.0;
@@ -60,8 +62,11 @@ static void launch_job(ServeJob *j) {
     Scratch ws(j->stream);
     cudaEventRecord(j->e0, j->stream);
     ds_status rc;
-    if (j->o.precision == DS_FP64) rc = enqueue_request<double>(M, &j->q, &j->o, (double *)j->out, j->stream, ws, &j->info);
-    else rc = enqueue_request<float>(M, &j->q, &j->o, (float *)j->out, j->stream, ws, &j->info);
+    const TaylorHint *h = j->has_hint ? &j->hint : nullptr;
+    if (j->o.precision == DS_FP64)
+        rc = enqueue_request<double>(M, &j->q, &j->o, (double *)j->out, j->stream, ws, &j->info, h);
+    else
+        rc = enqueue_request<float>(M, &j->q, &j->o, (float *)j->out, j->stream, ws, &j->info, h);
     cudaEventRecord(j->e1, j->stream);
     ws.release();
     if (rc == DS_OK && cudaLaunchHostFunc(j->stream, job_done, j) == cudaSuccess) return;
@@ -164,13 +169,17 @@ extern "C" ds_status ds_submit(ds_model *M, const ds_qgrid *q, const ds_opts *o,
     int P = o->taylor_order;
     if (o->disorder == DS_DISP && P < 0) {
         Scratch ws(ctx->stream);
-        rc = resolve_taylor_order(M, q, o, ctx->stream, ws, &P, &j->xmax);
+        double umax = 0.0;
+        rc = resolve_taylor_order(M, q, o, ctx->stream, ws, &P, &j->xmax, &umax);
         ws.release();
         if (rc != DS_OK) {
             delete j;
             return rc;
         }
-        j->o.taylor_order = P;
+        j->has_hint = true;
+        j->hint.P = P;
+        j->hint.xmax = j->xmax;
+        j->hint.umax = umax;
     }
     j->footprint = request_footprint(M, q, &j->o, P < 0 ? 0 : P);
     if (j->footprint > ctx->budget) {

@@ -207,6 +207,7 @@ ds_status subbox_run(ds_model *M, const ds_qgrid *q, const ds_opts *o, T *d_out,
     if (ws.total > ctx->budget)
         return ds_fail(ctx, DS_ERR_ADMISSION, "sub-box request needs %zu bytes of scratch, budget %zu", ws.total,
                        ctx->budget);
+    if (M->ready) cudaStreamWaitEvent(st, M->ready, 0);  // uploads made on another stream
     cudaMemcpyAsync(d_pairs, pairs.data(), sizeof(int2) * npair, cudaMemcpyHostToDevice, st);
     cudaMemcpyAsync(d_scat, M->scat.data(), sizeof(double) * nsite, cudaMemcpyHostToDevice, st);
     const bool diffuse = o->mode == DS_DIFFUSE;
@@ -251,7 +252,7 @@ ds_status subbox_run(ds_model *M, const ds_qgrid *q, const ds_opts *o, T *d_out,
     p.site_of = M->d_site_of;
     if constexpr (sizeof(T) == 4) p.ff = M->ff32;
     else p.ff = M->ff64;
-    memcpy(p.recip, M->recip, sizeof(p.recip));
+    set_reciprocal(p, M->recip, g.n);
     double norm = 1.0 / ((double)nmod * g.ncell * nsite * (double)nsb * nsb * nsb);
     if (kind == SRC_SPIN) norm *= 0.07265;  // C of Eq. mag_intensity (barn)
     p.norm = (T)norm;

@@ -70,6 +70,56 @@ def test_displacive_small_with_occupancy(ctx, prec, tag, mode):
     assert np.all(np.abs(got.reshape(-1) - I_dir) <= bound + 2 * TOL[tag] * peak)
 
 
+@pytest.mark.parametrize("prec,tag", PREC)
+@pytest.mark.parametrize("mode", [0, 1])
+def test_displacive_zone_orders_small(ctx, prec, tag, mode):
+    """Per-zone Taylor orders (taylor_zonal = 1): voxel by voxel equal to the oracle's zone-order
+    method, within the per-voxel remainder bound of the direct sum; the served request gives
+    the same bits."""
+    import torch
+    m = syn.small_case(syn.DISP, cells=(4, 6, 5), nsite=3, nmodels=2, seed=105, sigma=0.15)
+    lm = to_library(ctx, m)
+    q = qgrid_tuple(m.qgrid)
+    opts = dict(disorder=2, mode=mode, precision=prec, taylor_order=-1, taylor_eps=1e-6, taylor_zonal=1)
+    got, info = lm.intensity(q, **opts)
+    pv, P = core.zone_taylor_orders(m, m.qgrid, 1e-6)
+    assert info["taylor_order"] == P and len(np.unique(pv)) >= 2
+    want = core.displacive_intensity_fft(m, _G(m), mode, P=P, P_vox=pv)
+    assert rel_err_of_peak(got, want) < TOL[tag]
+    hkl = m.qgrid.hkl()
+    I_dir, F = core.displacive_intensity_direct(m, hkl, mode, return_F=True)
+    bound = core.truncation_bound(m, hkl, pv, mode, F=F)
+    assert np.all(np.abs(got.reshape(-1) - I_dir) <= bound + 2 * TOL[tag] * np.max(np.abs(I_dir)))
+    out = torch.empty(m.qgrid.count, dtype=torch.float64 if prec == 0 else torch.float32, device="cuda")
+    t = lm.submit(q, out, **opts)
+    ctx.wait(t, 60.0)
+    assert np.array_equal(out.cpu().numpy(), got)
+
+
+@pytest.mark.parametrize("prec,tag", PREC)
+def test_displacive_fcc_8cubed_zone_orders_full_volume(ctx, prec, tag):
+    """fcc 8^3, 64^3 voxels, per-zone orders at eps = 1e-8: the whole volume within the
+    per-voxel remainder bound of the exact direct sum; sampled voxels (Bragg positions
+    included) against the oracle's zone-order method."""
+    m = syn.displacive_fcc()
+    lm = to_library(ctx, m)
+    got, info = lm.intensity(qgrid_tuple(m.qgrid), disorder=2, mode=1, precision=prec, taylor_order=-1,
+                             taylor_eps=1e-8, taylor_zonal=1)
+    pv, P = core.zone_taylor_orders(m, m.qgrid, 1e-8)
+    assert info["taylor_order"] == P and pv.min() < P
+    hkl = m.qgrid.hkl()
+    I_dir, F = core.displacive_intensity_direct(m, hkl, 1, return_F=True)
+    bound = core.truncation_bound(m, hkl, pv, 1, F=F)
+    peak = np.max(I_dir)
+    assert np.all(np.abs(got.reshape(-1) - I_dir) <= bound + TOL[tag] * peak)
+    rng = np.random.default_rng(1)
+    G = _G(m)
+    idx = np.concatenate([rng.choice(G.shape[0], 400, replace=False),
+                          np.nonzero(np.all(np.mod(G, 8) == 0, axis=1))[0][:40]])
+    want = core.displacive_intensity_fft(m, G[idx], 1, P=P, P_vox=pv[idx])
+    assert np.max(np.abs(got.reshape(-1)[idx] - want)) < TOL[tag] * peak
+
+
 @pytest.mark.parametrize("cells", [(7, 9, 10), (12, 5, 8), (3, 14, 6), (16, 16, 16), (1, 1, 2), (2, 3, 1)])
 def test_fft_sizes_all_radices(ctx, cells):
     """Supercells with factors 2, 3, 4, 5, 7 and degenerate axes, FP64 parity."""
@@ -116,6 +166,30 @@ def test_device_output_on_torch_stream(ctx):
     s.synchronize()
     want = core.occupancy_intensity_fft(m, _G(m), 1)
     assert rel_err_of_peak(out.cpu().numpy(), want) < TOL["fp32"]
+
+
+def test_upload_on_one_stream_request_on_another(ctx):
+    """A device upload queued on one stream behind a long kernel, then a request on another
+    stream: the request waits for the upload (and the site means computed with it)."""
+    import torch
+    if not hasattr(torch.cuda, "_sleep"):
+        pytest.skip("torch.cuda._sleep not available")
+    m = syn.small_case(syn.SPIN, cells=(4, 5, 6), nsite=3, nmodels=1, seed=121)
+    lm = to_library(ctx, m)
+    q = qgrid_tuple(m.qgrid)
+    m.spins = syn.small_case(syn.SPIN, cells=(4, 5, 6), nsite=3, nmodels=1, seed=122).spins
+    new = torch.from_numpy(np.ascontiguousarray(m.spins)).cuda()
+    torch.cuda.synchronize()
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    with torch.cuda.stream(s1):
+        torch.cuda._sleep(20_000_000)
+        lm.upload_spins(new)
+    out = torch.empty(m.qgrid.count, dtype=torch.float64, device="cuda")
+    with torch.cuda.stream(s2):
+        lm.intensity(q, out=out, disorder=1, mode=1, precision=0)
+    torch.cuda.synchronize()
+    want = core.magnetic_intensity_fft(m, _G(m), 1)
+    assert rel_err_of_peak(out.cpu().numpy(), want) < TOL["fp64"]
 
 
 def test_errors_are_reported(ctx):
@@ -207,6 +281,45 @@ def test_grouped_sites_several_form_factor_classes(ctx, dis):
         assert rel_err_of_peak(got, want) < TOL[tag]
 
 
+def _special_positions_case(kind, nsite, ff, seed):
+    """Sites on multiples of 1/4, 1/3 and 1/2 along the three axes (zone phases periodic in H
+    with periods 4, 3, 2; suffix _xr: random first coordinates), a triclinic cell, two supercells and a ragged grid of 6 zones per
+    axis, so that the residue-class recombination applies."""
+    cells = (5, 6, 4)
+    q = syn.QGrid(h0=tuple(-3.0 + 3.0 / n for n in cells), step=tuple(1.0 / n for n in cells),
+                  count=tuple(6 * n - 5 for n in cells))
+    m = syn.small_case(kind, cells=cells, nsite=nsite, nmodels=2, seed=seed, qgrid=q)
+    rng = np.random.default_rng(seed)
+    m.sites = np.stack([rng.integers(0, 4, nsite) / 4.0, rng.integers(0, 3, nsite) / 3.0,
+                        rng.integers(0, 2, nsite) / 2.0 + rng.integers(-1, 2, nsite)], axis=1)
+    if ff.endswith("_xr"):  # no period along the first axis: every zone H1 its own class
+        m.sites[:, 0] = rng.random(nsite)
+    if ff.startswith("one_j0"):
+        m.ff_kind = np.full(nsite, syn.FF_J0, dtype=np.int32)
+        m.ff_coef = np.zeros((nsite, 9))
+        m.ff_coef[:, :7] = syn.J0_COEF
+    elif ff == "const":
+        m.ff_kind = np.zeros(nsite, dtype=np.int32)
+    return m
+
+
+@pytest.mark.parametrize("prec,tag", PREC)
+@pytest.mark.parametrize("disorder,nsite,ff,mode", [(0, 6, "mixed", 1), (0, 20, "const", 0), (0, 5, "one_j0", 1),
+                                                    (1, 6, "mixed", 0), (1, 7, "one_j0", 1), (1, 16, "const", 0),
+                                                    (1, 5, "one_j0_xr", 0), (0, 4, "mixed_xr", 1)])
+def test_residue_classes_special_positions(ctx, prec, tag, disorder, nsite, ff, mode):
+    """Sites on special positions: the zone phases repeat with H, and the library forms the site
+    sum once per residue class of zones; voxel by voxel equal to the oracle (Q = 0 included,
+    one or several form-factor classes, up to 20 sites)."""
+    m = _special_positions_case(disorder, nsite, ff, 200 + nsite)
+    G = _G(m)
+    assert np.any(np.all(G == 0, axis=1))
+    lm = to_library(ctx, m)
+    got, _ = lm.intensity(qgrid_tuple(m.qgrid), disorder=disorder, mode=mode, precision=prec)
+    fn = core.occupancy_intensity_fft if disorder == 0 else core.magnetic_intensity_fft
+    assert rel_err_of_peak(got, fn(m, G, mode)) < TOL[tag]
+
+
 @pytest.mark.parametrize("disorder,kind", [("occ", 0), ("spin", 1)])
 @pytest.mark.parametrize("nsb,mode", [(1, 1), (2, 0), (3, 1)])
 def test_subbox_against_brute_force(ctx, disorder, kind, nsb, mode):
@@ -289,3 +402,109 @@ def test_autograd_function_directional_derivative(ctx):
     fd = (vals[0] - vals[1]) / (2 * h)
     ad = float(np.sum(gu * v))
     assert abs(fd - ad) < 2e-3 * max(1.0, abs(ad))
+
+
+def test_fcc_32cubed_displacive_full_size():
+    """fcc 32^3 (131,072 atoms), u ~ N(0, 0.1^2), |h,k,l| <= 5 step 1/32 (321^3 voxels), Taylor
+    order by the remainder bound at eps = 1e-8: FP32 within 1e-5 of peak of the FP64 path on the
+    whole volume, and both within the bound of the exact direct sum on sampled voxels."""
+    import torch
+    m, _ = syn.differentiation_pair()
+    lm = to_library(ctx_holder(), m)
+    q = qgrid_tuple(m.qgrid)
+    o32 = torch.empty(m.qgrid.count, dtype=torch.float32, device="cuda")
+    o64 = torch.empty(m.qgrid.count, dtype=torch.float64, device="cuda")
+    _, info = lm.intensity(q, out=o32, disorder=2, mode=0, precision=1, taylor_order=-1, taylor_eps=1e-8)
+    lm.intensity(q, out=o64, disorder=2, mode=0, precision=0, taylor_order=-1, taylor_eps=1e-8)
+    torch.cuda.synchronize()
+    peak = float(o64.max())
+    assert float((o32.double() - o64).abs().max()) < 1e-5 * peak
+    P = info["taylor_order"]
+    assert P == core.taylor_order(core.x_max(m, m.qgrid), 1e-8)
+    idx = np.random.default_rng(7).choice(m.qgrid.nvox, 200, replace=False)
+    hkl = sample_G(m, idx) / 32.0
+    I_dir, F = core.displacive_intensity_direct(m, hkl, 0, return_F=True)
+    bound = core.truncation_bound(m, hkl, P, 0, F=F)
+    sel = torch.from_numpy(idx).cuda()
+    for out, tol in ((o64, 1e-10), (o32, 1e-5)):
+        got = out.reshape(-1)[sel].double().cpu().numpy()
+        assert np.all(np.abs(got - I_dir) <= bound + tol * peak)
+
+
+def test_fcc_32cubed_gradient_directional_derivative():
+    """Full-size adjoint: chi^2 against the correlated target model; <dchi2/du, v> from the
+    FP32 adjoint against the central difference of the FP64 forward along a random v."""
+    import torch
+    m, t = syn.differentiation_pair()
+    ctx = ctx_holder()
+    lm, lt = to_library(ctx, m), to_library(ctx, t)
+    q = qgrid_tuple(m.qgrid)
+    opts = dict(disorder=2, mode=0, taylor_order=-1, taylor_eps=1e-8)
+    It = torch.empty(m.qgrid.count, dtype=torch.float64, device="cuda")
+    lt.intensity(q, out=It, precision=0, **opts)
+    I = torch.empty(m.qgrid.count, dtype=torch.float64, device="cuda")
+    lm.intensity(q, out=I, precision=0, **opts)
+    dL = (2.0 * (I - It)).float().contiguous()
+    g = torch.empty(lm._shape(3), dtype=torch.float32, device="cuda")
+    lm.backward(q, dL, grad=g, precision=1, **opts)
+    v = torch.from_numpy(np.random.default_rng(3).standard_normal(m.disp.shape)).cuda()
+    h = 2e-4
+    chi = []
+    for sgn in (1, -1):
+        lm.upload_displacements(torch.from_numpy(m.disp.astype(np.float64)).cuda().add(sgn * h * v).float().contiguous())
+        lm.intensity(q, out=I, precision=0, **opts)
+        chi.append(float(((I - It) ** 2).sum()))
+    fd = (chi[0] - chi[1]) / (2 * h)
+    ad = float((g.double() * v).sum())
+    assert abs(fd - ad) < 2e-3 * abs(ad)
+
+
+def test_perovskite_64cubed_displacive_full_size():
+    """Perovskite 64^3 (1,310,720 atoms), correlated displacements, 4-Gaussian form factors,
+    |h,k,l| <= 8 step 1/64 (1025^3 voxels), FP32 with eps = 1e-5: sampled voxels against the
+    exact direct sum within the remainder bound + 1e-5 of peak; the Lanczos (m = 2, m' = 8)
+    volume at sampled voxels against the literal finite sum over direct-sum I(G)."""
+    import torch
+    m = syn.perovskite_correlated()
+    lm = to_library(ctx_holder(), m)
+    q = qgrid_tuple(m.qgrid)
+    out = torch.empty(m.qgrid.count, dtype=torch.float32, device="cuda")
+    _, info = lm.intensity(q, out=out, disorder=2, mode=1, precision=1, taylor_order=-1, taylor_eps=1e-5)
+    torch.cuda.synchronize()
+    peak = float(out.max())
+    P = info["taylor_order"]
+    idx = np.random.default_rng(11).choice(m.qgrid.nvox, 40, replace=False)
+    hkl = sample_G(m, idx) / 64.0
+    I_dir, F = core.displacive_intensity_direct(m, hkl, 1, return_F=True)
+    bound = core.truncation_bound(m, hkl, P, 1, F=F)
+    got = out.reshape(-1)[torch.from_numpy(idx).cuda()].double().cpu().numpy()
+    assert np.all(np.abs(got - I_dir) <= bound + 1e-5 * peak)
+    del out
+    torch.cuda.empty_cache()
+    sm = torch.empty(m.qgrid.count, dtype=torch.float32, device="cuda")
+    lm.intensity(q, out=sm, disorder=2, mode=1, precision=1, taylor_order=P, smoothing=1, lanczos_m=2,
+                 lanczos_mprime=8)
+    torch.cuda.synchronize()
+    pick = np.array([[512, 512, 512], [300, 700, 650], [64, 900, 512]])
+    Q = pick + sample_G(m, np.array([0]))[0]
+    IG = lambda Gs: core.displacive_intensity_direct(m, Gs / 64.0, 1)
+    want = noise.lanczos_resample(IG, Q.astype(np.float64), 2, 8)
+    got = np.array([float(sm[tuple(p)]) for p in pick])
+    assert np.all(np.abs(got - want) <= 1e-5 * float(sm.max()) + 1e-4 * np.abs(want))
+
+
+_CTX = []
+
+
+def sample_G(m, idx):
+    """Supercell indices G of the voxels `idx` of m.qgrid without building the whole grid."""
+    g0 = np.rint(np.array(m.qgrid.h0) * np.array(m.cells)).astype(np.int64)
+    ijk = np.stack(np.unravel_index(np.asarray(idx), m.qgrid.count), axis=1)
+    return g0[None, :] + ijk
+
+
+def ctx_holder():
+    import paper_1809_07088_gb300 as ds
+    if not _CTX:
+        _CTX.append(ds.Context(0))
+    return _CTX[0]
