@@ -7,10 +7,11 @@ vMF(kappa = 2) about seeded per-site axes, <j0> magnetic form factor (A=0.4 a=15
 c=1 D=0), Q grid |h|,|k|,|l| <= 6 in steps of 1/20 (241^3 = 13,997,521 voxels).  One step =
 the whole hot path for both volumes: per-site FFTs + recombination + |F|^2 (nuclear, diffuse
 mode) and per-site/per-component FFTs + recombination + perpendicular projection (magnetic,
-total mode), FP32 arithmetic.  Metric: intensity voxels/s (both volumes counted), checked
-against the FP64 path of the same kernels (<= 1e-5 of peak).
+total mode), FP32 arithmetic; the two independent volumes run on two streams (--streams 1:
+one after the other).  Metric: intensity voxels/s (both volumes counted), checked against the
+FP64 path of the same kernels (<= 1e-5 of peak).
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--streams 1|2]
 Under torchrun each rank runs an independent replica on its own GPU (the workload does not
 shard); rank 0 prints one JSON line.
 """
@@ -32,6 +33,11 @@ METRIC = "intensity voxels/s at <=1e-5 rel err vs plain FP64 GPU path"
 UNIT = "voxels/s"
 HMAX, NCELL, NSITE = 6.0, 20, 16
 FP32_FMA_LANES_PER_SM, NUM_SMS = 128, 152
+# dram__bytes_read.sum + dram__bytes_write.sum of one launch of the magnetic recombination on
+# this workload, from an ncu capture of the current kernel (profiles/); None when the kernel has
+# changed since the capture
+MAG_KERNEL_TRAFFIC = 21923072
+MAG_KERNEL_TRAFFIC_SOURCE = "ncu --set full capture, profiles/k_recomb_cm_res_pyrochlore_20cubed.md"
 
 
 def workload_config(extra=None):
@@ -247,9 +253,23 @@ def run_ours(args):
     I_m = torch.empty(m.qgrid.count, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
 
-    def step(prec=ds.DS_FP32, outs=(I_n, I_m)):
-        lm_n.intensity(q, out=outs[0], disorder=ds.DS_OCC, mode=ds.DS_DIFFUSE, precision=prec)
-        lm_m.intensity(q, out=outs[1], disorder=ds.DS_SPIN, mode=ds.DS_TOTAL, precision=prec)
+    side = [torch.cuda.Stream(dev), torch.cuda.Stream(dev)] if args.streams == 2 else None
+    fork, join = torch.cuda.Event(), [torch.cuda.Event(), torch.cuda.Event()]
+
+    def step(prec=ds.DS_FP32, outs=(I_n, I_m), single=False):
+        if side is None or single:
+            lm_n.intensity(q, out=outs[0], disorder=ds.DS_OCC, mode=ds.DS_DIFFUSE, precision=prec)
+            lm_m.intensity(q, out=outs[1], disorder=ds.DS_SPIN, mode=ds.DS_TOTAL, precision=prec)
+            return
+        # the two independent volumes on two streams, forked from and joined back to `stream`
+        fork.record(stream)
+        for s_, j_, (lm_, o_, dis, mode) in zip(side, join, ((lm_n, outs[0], ds.DS_OCC, ds.DS_DIFFUSE),
+                                                            (lm_m, outs[1], ds.DS_SPIN, ds.DS_TOTAL))):
+            s_.wait_event(fork)
+            with torch.cuda.stream(s_):
+                lm_.intensity(q, out=o_, disorder=dis, mode=mode, precision=prec)
+            j_.record(s_)
+            stream.wait_event(j_)
 
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     clocks = ClockSampler(local)
@@ -284,6 +304,17 @@ def run_ours(args):
     total_ms = max_over_ranks(sum(step_ms), dev)
     vox_step = 2 * nvox
     value = ws * vox_step * args.steps / (total_ms / 1e3)
+
+    # the dominant kernel timed alone as well (one stream, no overlap with the other volume)
+    ctx.lib.ds_profile_report(ctx.h, ctypes_buf, len(ctypes_buf))
+    ctx.lib.ds_profile_enable(ctx.h, 1)
+    for _ in range(20):
+        flush.zero_()
+        step(single=True)
+    torch.cuda.synchronize(dev)
+    ctx.lib.ds_profile_enable(ctx.h, 0)
+    ctx.check(ctx.lib.ds_profile_report(ctx.h, ctypes_buf, len(ctypes_buf)))
+    alone = json.loads(ctypes_buf.value.decode())["stages"].get("recombine_spin", {"count": 1, "ms": float("nan")})
 
     # accuracy of the timed FP32 path against the FP64 path of the same kernels
     I_n64 = torch.empty(m.qgrid.count, dtype=torch.float64, device=dev)
@@ -327,20 +358,25 @@ def run_ours(args):
            "h2d_bytes_per_step": int(occ_h.numel() * occ_h.element_size() + spin_h.numel() * spin_h.element_size()),
            "d2h_bytes_per_step": int(2 * nvox * 4)}
 
-    # roofline of the dominant kernel: the magnetic recombination (FP32 FMA pipe)
+    # roofline of the dominant kernel, the magnetic recombination (residue-class kernel): its
+    # algorithmic traffic is the intensity volume it writes (4 B per voxel) plus one read of the
+    # site spectra (nsite x 3 components x n1 n2 (n3/2 + 1) complex FP32); HBM bound
     peaks, peak_src = measured_peaks()
-    sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
-    alu_peak = NUM_SMS * FP32_FMA_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
     st = prof["stages"]
     rec = st.get("recombine_spin", {"count": 1, "ms": float("nan")})
     avg_ms = rec["ms"] / max(1, rec["count"])
-    flops = nvox * NSITE * 3 * 8              # complex multiply-adds of Eq. mag_sf per voxel
-    achieved = flops / (avg_ms / 1e3) / 1e12
-    roofline = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
-                "frac": achieved / alu_peak, "traffic": None, "kernel": "k_recomb_cm<float,3,16>",
-                "peak_source": "derived: %d SMs x %d FP32 lanes x 2 flop x %.0f MHz (sm_max_mhz, %s peaks file)"
-                               % (NUM_SMS, FP32_FMA_LANES_PER_SM, sm_mhz, peak_src),
-                "flops_per_launch": flops, "avg_launch_ms": avg_ms}
+    spec_bytes = NSITE * 3 * NCELL * NCELL * (NCELL // 2 + 1) * 8
+    alg_bytes = nvox * 4 + spec_bytes
+    achieved = alg_bytes / (avg_ms / 1e3) / 1e9
+    hbm = float(peaks["hbm_gbs"])
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                "traffic": MAG_KERNEL_TRAFFIC, "kernel": "k_recomb_cm_res<float,3,1,4,4,false,2>",
+                "peak_source": "%s HBM copy bandwidth (MEASURED_PEAKS.json hbm_gbs)" % peak_src,
+                "algorithmic_bytes_per_launch": alg_bytes, "avg_launch_ms": avg_ms,
+                "traffic_source": MAG_KERNEL_TRAFFIC_SOURCE,
+                "alone": {"avg_launch_ms": alone["ms"] / max(1, alone["count"]),
+                          "achieved": alg_bytes / (alone["ms"] / max(1, alone["count"]) / 1e3) / 1e9,
+                          "note": "same kernel timed on one stream without the other volume's kernels"}}
     stages = {k: {"count": v["count"], "avg_ms": v["ms"] / max(1, v["count"])} for k, v in st.items()}
 
     cpu = None
@@ -355,7 +391,8 @@ def run_ours(args):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": workload_config({"parallelism": "replicas" if ws > 1 else "single GPU"}),
+            "config": workload_config({"parallelism": "replicas" if ws > 1 else "single GPU",
+                                       "streams": args.streams}),
             "max_rel_err_vs_fp64": max(errs), "fp64_plain": {"ms_per_step": ms64, "value": ws * vox_step / (ms64 / 1e3)},
             "e2e": e2e, "roofline": roofline, "stages": stages, "gpu_launches": int(prof.get("launches", 0)),
             "wall_ms_per_step": 1e3 * t_wall / args.steps, "clocks": clk, "cpu_baseline": cpu,
@@ -498,6 +535,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serving", type=int, default=128, help="requests in the serving stream (0 = skip)")
+    ap.add_argument("--streams", type=int, default=2, choices=[1, 2],
+                    help="2: the two volumes of a step on two streams (their kernels overlap)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -94,6 +94,13 @@ __device__ __forceinline__ float exp2_w(float x) {
     asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
     return y;
 }
+// 1/x: the SFU's approximate reciprocal (PTX rcp.approx) in FP32, exact division in FP64
+__device__ __forceinline__ double rcp_w(double x) { return 1.0 / x; }
+__device__ __forceinline__ float rcp_w(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
 __device__ __forceinline__ double div_w(double a, double b) { return a / b; }
 __device__ __forceinline__ float div_w(float a, float b) { return __fdividef(a, b); }
 

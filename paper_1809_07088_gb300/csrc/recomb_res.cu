@@ -32,6 +32,7 @@ __device__ __forceinline__ int floor_div_r(int a, int b) {
 }
 
 constexpr int RES_THREADS = 128;
+constexpr int V3 = 4;  // voxels of a residue class along axis 3 handled without a loop
 
 // form factor of class c at |Q|^2 (Gaussian-sum form, coefficients read from the launch params);
 // NG >= 0: the number of Gaussians known at compile time, NG < 0: read from the params
@@ -46,18 +47,27 @@ __device__ __forceinline__ T ff_q2(const FormFactors<T> &ff, int c, T q2) {
 
 }  // namespace
 
+// form factor from register-held coefficients of one class (NG Gaussians)
+template <typename T, int NG>
+__device__ __forceinline__ T ff_regs(const T (&ga)[4], const T (&gb)[4], T gc, T q2) {
+    T f = gc;
+#pragma unroll
+    for (int i = 0; i < NG; ++i) f = fma(ga[i], exp2_w(gb[i] * q2), f);
+    return f;
+}
+
 // MAXC: form-factor classes handled (1: one class, its form factor applied to |F|^2); D3: rho3
 // classes formed per pass over the sites (their F stay in registers; Y is streamed, not kept);
 // ACC: add into the output (second and later supercells of the ensemble); NG: Gaussians of the
-// single form-factor class (MAXC = 1; 0 = constant form factor), -1 = read from the params
+// single form-factor class (MAXC = 1; 0 = constant form factor), -1 = read from the params.
+// Launch parameters used in the voxel loops are copied to registers first.
 template <typename T, int NC, int MAXC, int D3, int MINB, bool ACC, int NG>
 __global__ void __launch_bounds__(RES_THREADS, MINB)
     k_recomb_cm_res(const __grid_constant__ RecombParams<T> p, int s3) {
     using C = c_t<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const Geometry &g = p.g;
-    const GridMap &gm = p.gm;
     const int nsite = p.nsite;
+    const int n1 = p.g.n[0], n2 = p.g.n[1], n3 = p.g.n[2];
     const int d1 = p.dres[0], d2 = p.dres[1], d3 = p.dres[2];
     const int part = blockIdx.y % s3;
     const int r12 = blockIdx.y / s3;
@@ -72,18 +82,43 @@ __global__ void __launch_bounds__(RES_THREADS, MINB)
     __syncthreads();
 
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= g.ncell) return;
-    const int k3 = k % g.n[2];
-    const int k2 = (k / g.n[2]) % g.n[1];
-    const int k1 = k / (g.n[2] * g.n[1]);
+    if (k >= p.g.ncell) return;
+    const int k3 = k % n3;
+    const int k2 = (k / n3) % n2;
+    const int k1 = k / (n3 * n2);
+    const int g01 = p.gm.g0[0], g02 = p.gm.g0[1], g03 = p.gm.g0[2];
+    const int cnt1 = p.gm.cnt[0], cnt2 = p.gm.cnt[1], cnt3 = p.gm.cnt[2];
+    const int nH1 = p.gm.nH[0], nH2 = p.gm.nH[1];
+    // first voxel index along each axis of zone h: G = n (Hmin + h) + k
+    const int G1b = n1 * p.gm.Hmin[0] + k1, G2b = n2 * p.gm.Hmin[1] + k2, G3b = n3 * p.gm.Hmin[2] + k3;
     // zones along axis 3 whose voxel (H3, k3) lies in the grid
-    const int h3lo = max(-floor_div_r(-(gm.g0[2] - k3), g.n[2]) - gm.Hmin[2], 0);
-    const int h3hi = min(floor_div_r(gm.g0[2] + gm.cnt[2] - 1 - k3, g.n[2]) - gm.Hmin[2], gm.nH[2] - 1);
+    const int h3lo = max(-floor_div_r(-(g03 - G3b), n3), 0);
+    const int h3hi = min(floor_div_r(g03 + cnt3 - 1 - G3b, n3), p.gm.nH[2] - 1);
     int conj;
-    const int kidx = half_index(g, k1, k2, k3, conj);
-    const T c3[3] = {p.qstep[6], p.qstep[7], p.qstep[8]};
-    const T dG3 = (T)(g.n[2] * d3);  // G3 step between voxels of one residue class
+    const int kidx = half_index(p.g, k1, k2, k3, conj);
+    T qs[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) qs[i] = p.qstep[i];
+    T *const out = p.out;
+    const T norm = p.norm;
+    T fga[4], fgb[4], fgc = T(1);
+    if (MAXC == 1 && NG > 0) {
+        fgc = p.ff.cls_gc[0];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) fga[i] = p.ff.cls_ga[0][i], fgb[i] = p.ff.cls_gb[0][i];
+    }
+    const T dG3 = (T)(n3 * d3);  // G3 step between voxels of one residue class
+    T D[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) D[a] = qs[6 + a] * dG3;
+    const int stride = n3 * d3;
     const int nchunk = (d3 + D3 - 1) / D3;
+    const int h3lo_mod = h3lo % d3;
+    const int *const site_of = p.site_of;
+    const C *const phk = p.phk;
+    const T *const scat = p.scat;
+    const int nmax = p.nmax, ncell_h = p.g.ncell_h;
+    const C *const spec = p.spec + (size_t)p.model * nsite * NC * ncell_h + kidx;
 
     for (int ch = part; ch < nchunk; ch += s3) {
         const int r0 = ch * D3;
@@ -96,15 +131,16 @@ __global__ void __launch_bounds__(RES_THREADS, MINB)
 #pragma unroll
                 for (int c = 0; c < NC; ++c) F[r][cl][c] = mk<T>(T(0), T(0));
         int cls = 0;
+#pragma unroll 2
         for (int s = 0; s < nsite; ++s) {
             if (MAXC > 1 && s == p.ff.cls_end[cls]) ++cls;
-            const int site = p.site_of[s];
-            const C *t = p.phk + (size_t)site * 3 * p.nmax;
-            const C ph = cscale(cmul(cmul(t[k1], t[p.nmax + k2]), t[2 * p.nmax + k3]), p.scat[site]);
+            const int site = site_of[s];
+            const C *t = phk + site * 3 * nmax;
+            const C ph = cscale(cmul(cmul(t[k1], t[nmax + k2]), t[2 * nmax + k3]), scat[site]);
             C y[NC];
 #pragma unroll
             for (int c = 0; c < NC; ++c) {
-                C x = p.spec[(((size_t)p.model * nsite + site) * NC + c) * g.ncell_h + kidx];
+                C x = spec[(size_t)(site * NC + c) * ncell_h];
                 if (conj) x = cconj(x);
                 y[c] = cmul(ph, x);
             }
@@ -124,45 +160,66 @@ __global__ void __launch_bounds__(RES_THREADS, MINB)
         for (int r = 0; r < D3; ++r) {
             const int rho3 = r0 + r;
             if (rho3 >= d3) break;
-            const int h3s = h3lo + ((rho3 - h3lo) % d3 + d3) % d3;  // first zone of the class >= h3lo
+            int t3 = rho3 - h3lo_mod;
+            if (t3 < 0) t3 += d3;
+            const int h3s = h3lo + t3;  // first zone of the class >= h3lo
             if (h3s > h3hi) continue;
-            const int nv3 = (h3hi - h3s) / d3 + 1;                   // voxels of the class along axis 3
-            T tot1 = T(0);  // one class: |F|^2 is the same for every voxel of the residue class
+            const int nv3 = (h3hi - h3s) / d3 + 1;  // voxels of the class along axis 3
+            // one class: |F|^2 (times the norm), and the part of Q.F that varies along axis 3,
+            // are the same for every voxel of the residue class
+            T tot1 = T(0), dpr = T(0), dpi = T(0);
             if (MAXC == 1) {
 #pragma unroll
                 for (int c = 0; c < NC; ++c) tot1 += F[r][0][c].x * F[r][0][c].x + F[r][0][c].y * F[r][0][c].y;
-            }
-            const int G3s = g.n[2] * (gm.Hmin[2] + h3s) + k3;
-            for (int h1 = rho1; h1 < gm.nH[0]; h1 += d1) {
-                const int G1 = g.n[0] * (gm.Hmin[0] + h1) + k1;
-                if (G1 < gm.g0[0] || G1 >= gm.g0[0] + gm.cnt[0]) continue;
-                for (int h2 = rho2; h2 < gm.nH[1]; h2 += d2) {
-                    const int G2 = g.n[1] * (gm.Hmin[1] + h2) + k2;
-                    if (G2 < gm.g0[1] || G2 >= gm.g0[1] + gm.cnt[1]) continue;
-                    T Q12[3];
+                tot1 *= norm;
+                if (NC == 3) {
 #pragma unroll
-                    for (int a = 0; a < 3; ++a) Q12[a] = fma((T)G1, p.qstep[a], (T)G2 * p.qstep[3 + a]);
-                    T *dst = p.out + ((size_t)(G1 - gm.g0[0]) * gm.cnt[1] + (G2 - gm.g0[1])) * gm.cnt[2] +
-                             (G3s - gm.g0[2]);
-                    T G3f = (T)G3s;
-                    const int stride = g.n[2] * d3;
-                    for (int i3 = 0; i3 < nv3; ++i3, G3f += dG3, dst += stride) {
+                    for (int c = 0; c < 3; ++c) {
+                        dpr = fma(D[c], F[r][0][c].x, dpr);
+                        dpi = fma(D[c], F[r][0][c].y, dpi);
+                    }
+                }
+            }
+            const T tot23 = T(2) / T(3) * tot1;
+            const int G3s = G3b + n3 * h3s;
+            for (int h1 = rho1; h1 < nH1; h1 += d1) {
+                const int G1 = G1b + n1 * h1;
+                if (G1 < g01 || G1 >= g01 + cnt1) continue;
+                for (int h2 = rho2; h2 < nH2; h2 += d2) {
+                    const int G2 = G2b + n2 * h2;
+                    if (G2 < g02 || G2 >= g02 + cnt2) continue;
+                    // Q of the first voxel of the class in this column, and Q.F there
+                    T Qs[3];
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) Qs[a] = fma((T)G3s, qs[6 + a], fma((T)G1, qs[a], (T)G2 * qs[3 + a]));
+                    T pr0 = T(0), pi0 = T(0);
+                    if (MAXC == 1 && NC == 3) {
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) {
+                            pr0 = fma(Qs[c], F[r][0][c].x, pr0);
+                            pi0 = fma(Qs[c], F[r][0][c].y, pi0);
+                        }
+                    }
+                    T *const row = out + ((size_t)(G1 - g01) * cnt2 + (G2 - g02)) * cnt3 + (G3s - g03);
+                    // voxel i3 of the class along axis 3: G3 = G3s + i3 n3 d3
+                    auto voxel = [&](int i3) {
+                        const T t = (T)i3;
                         T Qv[3];
 #pragma unroll
-                        for (int a = 0; a < 3; ++a) Qv[a] = fma(G3f, c3[a], Q12[a]);
-                        const T q2 = Qv[0] * Qv[0] + Qv[1] * Qv[1] + Qv[2] * Qv[2];
-                        T I;
+                        for (int a = 0; a < 3; ++a) Qv[a] = fma(t, D[a], Qs[a]);
+                        const T q2 = fma(Qv[0], Qv[0], fma(Qv[1], Qv[1], Qv[2] * Qv[2]));
+                        T val;
                         if (MAXC == 1) {
-                            I = tot1;
+                            val = tot1;
                             if (NC == 3) {
-                                const T pr = Qv[0] * F[r][0][0].x + Qv[1] * F[r][0][1].x + Qv[2] * F[r][0][2].x;
-                                const T pi = Qv[0] * F[r][0][0].y + Qv[1] * F[r][0][1].y + Qv[2] * F[r][0][2].y;
-                                const T proj = div_w(pr * pr + pi * pi, q2);
-                                I = q2 > T(0) ? tot1 - proj : T(2) / T(3) * tot1;
+                                // |F_perp|^2 = |F|^2 - |Q.F|^2 / |Q|^2; (2/3)|F|^2 at Q = 0
+                                const T pr = fma(t, dpr, pr0), pi = fma(t, dpi, pi0);
+                                const T proj = fma(pr, pr, pi * pi) * (norm * rcp_w(q2));
+                                val = q2 > T(0) ? tot1 - proj : tot23;
                             }
-                            if (NG != 0) {
-                                const T f = ff_q2<T, NG>(p.ff, 0, q2);
-                                I *= f * f;
+                            if (NG > 0) {
+                                const T f = ff_regs<T, (NG > 0 ? NG : 0)>(fga, fgb, fgc, q2);
+                                val *= f * f;
                             }
                         } else {
                             C Fv[NC];
@@ -182,17 +239,22 @@ __global__ void __launch_bounds__(RES_THREADS, MINB)
                             T tot = T(0);
 #pragma unroll
                             for (int c = 0; c < NC; ++c) tot += Fv[c].x * Fv[c].x + Fv[c].y * Fv[c].y;
-                            I = tot;
+                            val = tot;
                             if (NC == 3) {
                                 const T pr = Qv[0] * Fv[0].x + Qv[1] * Fv[1].x + Qv[2] * Fv[2].x;
                                 const T pi = Qv[0] * Fv[0].y + Qv[1] * Fv[1].y + Qv[2] * Fv[2].y;
-                                I = q2 > T(0) ? tot - div_w(pr * pr + pi * pi, q2) : T(2) / T(3) * tot;
+                                val = q2 > T(0) ? tot - div_w(pr * pr + pi * pi, q2) : T(2) / T(3) * tot;
                             }
+                            val *= norm;
                         }
-                        const T val = p.norm * I;
+                        T *dst = row + i3 * stride;
                         if (ACC) *dst += val;
                         else *dst = val;
-                    }
+                    };
+#pragma unroll
+                    for (int i3 = 0; i3 < V3; ++i3)
+                        if (i3 < nv3) voxel(i3);
+                    for (int i3 = V3; i3 < nv3; ++i3) voxel(i3);
                 }
             }
         }
@@ -248,7 +310,7 @@ template <typename T> bool recombine_cm_residues(const RecombParams<T> &p, cudaS
         if (p.ff.ncls == 1) launch_res_one<T, 1, 4, dbl ? 2 : 8>(p, s);
         else launch_res_acc<T, 1, 4, 2, dbl ? 2 : 6, -1>(p, s);
     } else {
-        if (p.ff.ncls == 1) launch_res_one<T, 3, 4, dbl ? 2 : 8>(p, s);
+        if (p.ff.ncls == 1) launch_res_one<T, 3, 4, dbl ? 2 : 4>(p, s);
         else launch_res_acc<T, 3, 4, 2, dbl ? 2 : 4, -1>(p, s);
     }
     return true;

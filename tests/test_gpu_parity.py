@@ -130,6 +130,16 @@ def test_fft_sizes_all_radices(ctx, cells):
     assert rel_err_of_peak(got, want) < TOL["fp64"]
 
 
+@pytest.mark.parametrize("prec,tag", PREC)
+def test_fft_two_pass_radices(ctx, prec, tag):
+    """A supercell too large for the whole-field FFT kernel (30 x 28 x 35: radices 2, 3, 4, 5, 7)
+    goes through the two-pass plane/column FFT; parity with the oracle."""
+    m = syn.small_case(syn.OCC, cells=(30, 28, 35), nsite=2, nmodels=1, seed=105)
+    lm = to_library(ctx, m)
+    got, _ = lm.intensity(qgrid_tuple(m.qgrid), disorder=0, mode=1, precision=prec)
+    assert rel_err_of_peak(got, core.occupancy_intensity_fft(m, _G(m), 1)) < TOL[tag]
+
+
 def test_single_voxel_and_single_zone_grids(ctx):
     m = syn.small_case(syn.SPIN, cells=(4, 4, 4), nsite=2, nmodels=1, seed=105)
     lm = to_library(ctx, m)
