@@ -14,6 +14,7 @@ Contents, each function citing the passage it follows:
                                  total_sf_taylor, U_fft, A_fft, mag_ft (the method, "part 2");
                                  numpy's FFT is the library step
   core.monomials, taylor_order, x_max, truncation_bound ..... Section III C
+  core.zone_taylor_orders ...... the Section III C bound applied per zone H (|Q.u| <= |Q||u|)
   noise.subbox_intensity ....... Section V A, every lattice point an origin, brute force
   noise.lanczos_resample ....... Section V B, Eqs. intensity_convol_finite, weight_sinc,
                                  windowed_sinc, lanczos, and the 1/m' variant
@@ -22,7 +23,8 @@ Contents, each function citing the passage it follows:
 Pins (tests/test_oracle_*.py, all `-m "not gpu"`): brute-force double sum (Eq.
 intensity_dble_sum), Bragg-only closed forms of the undisplaced fcc crystal, Friedel symmetry,
 Parseval, invariance under supercell translations, the O(n^6) DFT, the Gaussian (Laue)
-closed form, the Taylor remainder bound, the 55-FFT count of the fifth-order example,
+closed form, the Taylor remainder bound (one order, and per-zone orders against a brute-force
+per-atom check and per-order reruns), the 55-FFT count of the fifth-order example,
 magnetic projection special cases, the Lanczos m = 2 weights, sub-box closed forms at
 n_sb = 1 and an independent pair-sum form, finite differences of the gradient, and the golden
 values under tests/golden/.  No function here is "parity unpinned".
