@@ -695,82 +695,86 @@ __device__ __forceinline__ ZoneBox zone_box(const Geometry &g, const GridMap &gm
 }
 
 // one chunk of monomials for one warp; CONJ: the warp's k reads the mirrored half spectrum;
-// MASK: a voxel takes only the monomials of order n <= its zone's order pzv[j]
-template <typename T, int MAXS, int ZPT, bool CONJ, bool MASK>
-__device__ __forceinline__ void disp_chunk(const c_t<T> *wt, const int *tinfo, int tc, int nsite, const T (&qx)[ZPT],
-                                           const T (&qy)[ZPT], const T (&qz)[ZPT], const int (&pzv)[ZPT],
-                                           T (&ca)[ZPT], T (&cb)[ZPT], T (&cc)[ZPT], c_t<T> (&S)[ZPT][MAXS]) {
+// MASK: a voxel takes only the monomials of order n <= its zone's order pzv[j].  The update code
+// and the order of a monomial are the same for the whole warp, so each is a uniform branch and
+// the per-voxel work is one coefficient multiply and 2 NS multiply-adds.
+// Coefficient arithmetic of the Taylor recombination.  FP32 keeps the running coefficient of the
+// current monomial as a duplicated pair (c, c), so that S += c m is one paired FMA (FFMA2) on
+// the complex S and the coefficient update one paired multiply; FP64 uses scalars.
+template <typename T> struct CoefPair { using type = T; };
+template <> struct CoefPair<float> { using type = float2; };
+__device__ __forceinline__ float2 pair_of(float v) { return make_float2(v, v); }
+__device__ __forceinline__ double pair_of(double v) { return v; }
+__device__ __forceinline__ float2 pair_mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ double pair_mul(double a, double b) { return a * b; }
+__device__ __forceinline__ void pair_acc(float2 &S, float2 w, float2 m) { S = __ffma2_rn(w, m, S); }
+__device__ __forceinline__ void pair_acc(double2 &S, double w, double2 m) {
+    S.x = fma(w, m.x, S.x);
+    S.y = fma(w, m.y, S.y);
+}
+
+// one chunk of monomials for one warp; MASK: a voxel takes only the monomials of order
+// n <= its zone's order pzv[j].  The update code and the order of a monomial are the same for the
+// whole warp (uniform branches); per voxel and monomial the work is one coefficient multiply and
+// NS complex multiply-adds.
+template <typename T, int NS, int ZPT, bool MASK>
+__device__ __forceinline__ void disp_chunk(const c_t<T> *wt, const int *tinfo, int tc, const T (&qx)[ZPT],
+                                           const T (&qy)[ZPT], const typename CoefPair<T>::type (&qzp)[ZPT],
+                                           const int (&pzv)[ZPT], T (&ca)[ZPT], T (&cb)[ZPT],
+                                           typename CoefPair<T>::type (&ccp)[ZPT], c_t<T> (&S)[ZPT][NS]) {
+    using P = typename CoefPair<T>::type;
     for (int tt = 0; tt < tc; ++tt) {
         const int info = tinfo[tt];
         const int op = info & 3;
         const int n = info >> 2;
-        T w[ZPT];
+        if (op == OP_MULZ) {
 #pragma unroll
-        for (int j = 0; j < ZPT; ++j) {
-            if (op == OP_MULZ) {
-                cc[j] *= qz[j];
-            } else if (op == OP_NEWB) {
+            for (int j = 0; j < ZPT; ++j) ccp[j] = pair_mul(ccp[j], qzp[j]);
+        } else if (op == OP_NEWB) {
+#pragma unroll
+            for (int j = 0; j < ZPT; ++j) {
                 cb[j] *= qy[j];
-                cc[j] = cb[j];
-            } else if (op == OP_NEWA) {
+                ccp[j] = pair_of(cb[j]);
+            }
+        } else if (op == OP_NEWA) {
+#pragma unroll
+            for (int j = 0; j < ZPT; ++j) {
                 ca[j] *= qx[j];
                 cb[j] = ca[j];
-                cc[j] = ca[j];
-            } else {
-                ca[j] = cb[j] = cc[j] = T(1);
+                ccp[j] = pair_of(ca[j]);
             }
-            w[j] = (!MASK || n <= pzv[j]) ? cc[j] : T(0);
+        } else {
+#pragma unroll
+            for (int j = 0; j < ZPT; ++j) {
+                ca[j] = cb[j] = T(1);
+                ccp[j] = pair_of(T(1));
+            }
         }
-        if (!CONJ) {
+        P w[ZPT];
 #pragma unroll
-            for (int s = 0; s < MAXS; ++s) {
-                if (s < nsite) {
-                    const c_t<T> m = wt[(size_t)s * DISP_TC + tt];
+        for (int j = 0; j < ZPT; ++j) w[j] = (!MASK || n <= pzv[j]) ? ccp[j] : pair_of(T(0));
+        const c_t<T> *mt = wt + tt;
 #pragma unroll
-                    for (int j = 0; j < ZPT; ++j) {
-                        S[j][s].x = fma(w[j], m.x, S[j][s].x);
-                        S[j][s].y = fma(w[j], m.y, S[j][s].y);
-                    }
-                }
-            }
-        } else if (n & 1) {  // odd order: value (-x, +y)
+        for (int s = 0; s < NS; ++s) {
+            const c_t<T> m = mt[s * DISP_TC];
 #pragma unroll
-            for (int s = 0; s < MAXS; ++s) {
-                if (s < nsite) {
-                    const c_t<T> m = wt[(size_t)s * DISP_TC + tt];
-#pragma unroll
-                    for (int j = 0; j < ZPT; ++j) {
-                        S[j][s].x = fma(-w[j], m.x, S[j][s].x);
-                        S[j][s].y = fma(w[j], m.y, S[j][s].y);
-                    }
-                }
-            }
-        } else {  // even order: value (+x, -y)
-#pragma unroll
-            for (int s = 0; s < MAXS; ++s) {
-                if (s < nsite) {
-                    const c_t<T> m = wt[(size_t)s * DISP_TC + tt];
-#pragma unroll
-                    for (int j = 0; j < ZPT; ++j) {
-                        S[j][s].x = fma(w[j], m.x, S[j][s].x);
-                        S[j][s].y = fma(-w[j], m.y, S[j][s].y);
-                    }
-                }
-            }
+            for (int j = 0; j < ZPT; ++j) pair_acc(S[j][s], w[j], m);
         }
     }
 }
 
-template <typename T, int MAXS, int ZPT>
-__global__ void __launch_bounds__(DISP_KT * 32) k_recomb_disp(const __grid_constant__ RecombParams<T> p) {
+// NS: sites held per thread (the tile keeps NS rows; rows beyond nsite are zero); MINB: CTAs per
+// SM the register budget is sized for
+template <typename T, int NS, int ZPT, int MINB>
+__global__ void __launch_bounds__(DISP_KT * 32, MINB) k_recomb_disp(const __grid_constant__ RecombParams<T> p) {
     using C = c_t<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ int kidx_s[DISP_KT], kconj_s[DISP_KT], site_s[MAXS];
+    __shared__ int kidx_s[DISP_KT], kconj_s[DISP_KT], site_s[NS];
     const Geometry &g = p.g;
     const GridMap &gm = p.gm;
     const int nsite = p.nsite, nT = p.nT;
-    const size_t stage_elems = (size_t)DISP_KT * nsite * DISP_TC;
-    C *tile = (C *)smem_raw;                                   // [2][KT][nsite][TC]
+    const size_t stage_elems = (size_t)DISP_KT * NS * DISP_TC;
+    C *tile = (C *)smem_raw;                                   // [2][KT][NS][TC]
     int *tinfo = (int *)(tile + 2 * stage_elems);              // [2][TC]: op | n << 2
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int k0 = blockIdx.x * DISP_KT;
@@ -785,7 +789,7 @@ __global__ void __launch_bounds__(DISP_KT * 32) k_recomb_disp(const __grid_const
         kidx_s[threadIdx.x] = ki;
         kconj_s[threadIdx.x] = cj;
     }
-    if (threadIdx.x < MAXS && threadIdx.x < nsite) site_s[threadIdx.x] = p.site_of[threadIdx.x];
+    if (threadIdx.x < NS) site_s[threadIdx.x] = threadIdx.x < nsite ? p.site_of[threadIdx.x] : -1;
     __syncthreads();
 
     const bool kvalid = k < g.ncell;
@@ -795,32 +799,43 @@ __global__ void __launch_bounds__(DISP_KT * 32) k_recomb_disp(const __grid_const
     const int nzk = kvalid ? zb.n[0] * zb.n[1] * zb.n[2] : 0;
     const int zbase = blockIdx.y * (32 * ZPT);
     const bool active = zbase < nzk;  // warp-uniform
+    // a k of the other half of the spectrum reads the stored i^n M(-k); i^n M(k) = (-1)^n conj of it,
+    // and (-1)^n c_t(Q) = c_t(-Q): such a warp runs with -Q and conjugates its sums at the end
     const bool conj = kconj_s[warp] != 0;
+    const T qsign = conj ? T(-1) : T(1);
 
-    T qx[ZPT], qy[ZPT], qz[ZPT], ca[ZPT], cb[ZPT], cc[ZPT];
-    int Gz[ZPT][3];
-#pragma unroll
-    for (int j = 0; j < ZPT; ++j) {
+    using CP = typename CoefPair<T>::type;
+    T qx[ZPT], qy[ZPT], qz[ZPT], ca[ZPT], cb[ZPT];
+    CP qzp[ZPT], ccp[ZPT];
+    // supercell index G of this lane's voxel j (recomputed where needed to save registers)
+    auto voxel_G = [&](int j, int (&G)[3]) {
         int z = zbase + lane + 32 * j;
         if (z >= nzk) z = 0;  // computed but never stored
         const int nz23 = max(1, zb.n[1] * zb.n[2]);
         const int i1 = z / nz23, rem = z - i1 * nz23;
         const int i2 = rem / max(1, zb.n[2]), i3 = rem - i2 * max(1, zb.n[2]);
-        Gz[j][0] = g.n[0] * (zb.lo[0] + i1) + k1;
-        Gz[j][1] = g.n[1] * (zb.lo[1] + i2) + k2;
-        Gz[j][2] = g.n[2] * (zb.lo[2] + i3) + k3;
+        G[0] = g.n[0] * (zb.lo[0] + i1) + k1;
+        G[1] = g.n[1] * (zb.lo[1] + i2) + k2;
+        G[2] = g.n[2] * (zb.lo[2] + i3) + k3;
+    };
+#pragma unroll
+    for (int j = 0; j < ZPT; ++j) {
+        int Gj[3];
+        voxel_G(j, Gj);
         double Qd[3];
-        q_of_G(p.recip, g.n, Gz[j][0], Gz[j][1], Gz[j][2], Qd);
-        qx[j] = (T)(Qd[0] / p.qscale);
-        qy[j] = (T)(Qd[1] / p.qscale);
-        qz[j] = (T)(Qd[2] / p.qscale);
-        ca[j] = cb[j] = cc[j] = T(1);
+        q_of_G(p.recip, g.n, Gj[0], Gj[1], Gj[2], Qd);
+        qx[j] = qsign * (T)(Qd[0] / p.qscale);
+        qy[j] = qsign * (T)(Qd[1] / p.qscale);
+        qz[j] = qsign * (T)(Qd[2] / p.qscale);
+        qzp[j] = pair_of(qz[j]);
+        ca[j] = cb[j] = T(1);
+        ccp[j] = pair_of(T(1));
     }
-    C S[ZPT][MAXS];
+    C S[ZPT][NS];
 #pragma unroll
     for (int j = 0; j < ZPT; ++j)
 #pragma unroll
-        for (int s = 0; s < MAXS; ++s) S[j][s] = mk<T>(T(0), T(0));
+        for (int s = 0; s < NS; ++s) S[j][s] = mk<T>(T(0), T(0));
 
     // Taylor order of this CTA: the largest zone order among its voxels (all orders when no
     // per-zone table is given); its monomials are the order-Pc sub-simplex in lexicographic order
@@ -838,9 +853,11 @@ __global__ void __launch_bounds__(DISP_KT * 32) k_recomb_disp(const __grid_const
         for (int j = 0; j < ZPT; ++j) {
             pzv[j] = 0;
             if (zbase + lane + 32 * j < nzk) {
-                const int h1 = (Gz[j][0] - k1) / g.n[0] - gm.Hmin[0];
-                const int h2 = (Gz[j][1] - k2) / g.n[1] - gm.Hmin[1];
-                const int h3 = (Gz[j][2] - k3) / g.n[2] - gm.Hmin[2];
+                int Gj[3];
+                voxel_G(j, Gj);
+                const int h1 = (Gj[0] - k1) / g.n[0] - gm.Hmin[0];
+                const int h2 = (Gj[1] - k2) / g.n[1] - gm.Hmin[1];
+                const int h3 = (Gj[2] - k3) / g.n[2] - gm.Hmin[2];
                 pzv[j] = p.pzone[((size_t)h1 * gm.nH[1] + h2) * gm.nH[2] + h3];
                 pm = max(pm, pzv[j]);
             }
@@ -857,13 +874,13 @@ __global__ void __launch_bounds__(DISP_KT * 32) k_recomb_disp(const __grid_const
     auto load_chunk = [&](int stage, int t0) {
         const int tc = min(DISP_TC, nTc - t0);
         C *dst = tile + stage * stage_elems;
-        for (int idx = threadIdx.x; idx < DISP_KT * nsite * DISP_TC; idx += blockDim.x) {
+        for (int idx = threadIdx.x; idx < DISP_KT * NS * DISP_TC; idx += blockDim.x) {
             const int kk = idx % DISP_KT;
             const int rest = idx / DISP_KT;
             const int tt = rest % DISP_TC, s = rest / DISP_TC;
-            C *d = dst + ((size_t)kk * nsite + s) * DISP_TC + tt;
+            C *d = dst + ((size_t)kk * NS + s) * DISP_TC + tt;
             const int ki = kidx_s[kk];
-            if (tt < tc && ki >= 0) {
+            if (tt < tc && ki >= 0 && s < nsite) {
                 const int t = tmap ? tmap[t0 + tt] : t0 + tt;
                 cp_async<sizeof(C)>(d, p.spec + (((size_t)p.model * nsite + site_s[s]) * nT + t) * g.ncell_h + ki);
             } else {
@@ -891,26 +908,29 @@ __global__ void __launch_bounds__(DISP_KT * 32) k_recomb_disp(const __grid_const
         if (active) {
             const int stage = c & 1;
             const int tc = min(DISP_TC, nTc - c * DISP_TC);
-            const C *wt = tile + stage * stage_elems + (size_t)warp * nsite * DISP_TC;
+            const C *wt = tile + stage * stage_elems + (size_t)warp * NS * DISP_TC;
             const int *ti = tinfo + stage * DISP_TC;
-            if (p.pzone) {
-                if (conj) disp_chunk<T, MAXS, ZPT, true, true>(wt, ti, tc, nsite, qx, qy, qz, pzv, ca, cb, cc, S);
-                else disp_chunk<T, MAXS, ZPT, false, true>(wt, ti, tc, nsite, qx, qy, qz, pzv, ca, cb, cc, S);
-            } else {
-                if (conj) disp_chunk<T, MAXS, ZPT, true, false>(wt, ti, tc, nsite, qx, qy, qz, pzv, ca, cb, cc, S);
-                else disp_chunk<T, MAXS, ZPT, false, false>(wt, ti, tc, nsite, qx, qy, qz, pzv, ca, cb, cc, S);
-            }
+            if (p.pzone) disp_chunk<T, NS, ZPT, true>(wt, ti, tc, qx, qy, qzp, pzv, ca, cb, ccp, S);
+            else disp_chunk<T, NS, ZPT, false>(wt, ti, tc, qx, qy, qzp, pzv, ca, cb, ccp, S);
         }
         __syncthreads();
     }
     if (!active) return;
+    if (conj) {
+#pragma unroll
+        for (int j = 0; j < ZPT; ++j)
+#pragma unroll
+            for (int s = 0; s < NS; ++s) S[j][s].y = -S[j][s].y;
+    }
 
     // epilogue: F = sum_mu b f(|G|) exp(iG.r_mu) S_mu, minus <F(H)> at k = 0, I = |F|^2 norm
 #pragma unroll
     for (int j = 0; j < ZPT; ++j) {
         const int z = zbase + lane + 32 * j;
         if (z >= nzk) continue;
-        const int G1 = Gz[j][0], G2 = Gz[j][1], G3 = Gz[j][2];
+        int Gj[3];
+        voxel_G(j, Gj);
+        const int G1 = Gj[0], G2 = Gj[1], G3 = Gj[2];
         const T q2 = (T)(p.qscale * p.qscale) * (qx[j] * qx[j] + qy[j] * qy[j] + qz[j] * qz[j]);
         const T s2 = q2 * (T)(1.0 / (FOUR_PI_D * FOUR_PI_D));
         const int H1 = (G1 - k1) / g.n[0], H2 = (G2 - k2) / g.n[1], H3 = (G3 - k3) / g.n[2];
@@ -918,7 +938,7 @@ __global__ void __launch_bounds__(DISP_KT * 32) k_recomb_disp(const __grid_const
         C F = mk<T>(T(0), T(0)), part = mk<T>(T(0), T(0));
         int cls = 0;
 #pragma unroll
-        for (int s = 0; s < MAXS; ++s) {
+        for (int s = 0; s < NS; ++s) {
             if (s < nsite) {
                 const int site = site_s[s];
                 const C *tH = p.phH + (size_t)site * 3 * p.nHmax;
@@ -948,24 +968,33 @@ __global__ void __launch_bounds__(DISP_KT * 32) k_recomb_disp(const __grid_const
     }
 }
 
-template <typename T, int MAXS, int ZPT> static void launch_disp(const RecombParams<T> &p, cudaStream_t s) {
+template <typename T, int NS, int ZPT, int MINB> static void launch_disp(const RecombParams<T> &p, cudaStream_t s) {
     using C = c_t<T>;
     // the largest per-k zone box bounds the zone chunks
     int nzmax = 1;
     for (int a = 0; a < 3; ++a) nzmax *= (p.gm.cnt[a] + p.g.n[a] - 1) / p.g.n[a] + 1;
     dim3 grid((p.g.ncell + DISP_KT - 1) / DISP_KT, (nzmax + 32 * ZPT - 1) / (32 * ZPT));
-    const size_t sm = 2 * (size_t)DISP_KT * p.nsite * DISP_TC * sizeof(C) + 2 * DISP_TC * sizeof(int);
+    const size_t sm = 2 * (size_t)DISP_KT * NS * DISP_TC * sizeof(C) + 2 * DISP_TC * sizeof(int);
     if (sm > 48 * 1024)
-        cudaFuncSetAttribute(k_recomb_disp<T, MAXS, ZPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    k_recomb_disp<T, MAXS, ZPT><<<grid, DISP_KT * 32, sm, s>>>(p);
+        cudaFuncSetAttribute(k_recomb_disp<T, NS, ZPT, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_recomb_disp<T, NS, ZPT, MINB><<<grid, DISP_KT * 32, sm, s>>>(p);
     count_launches(1);
 }
 
+// sites per thread: exact for 1..8 sites (no idle rows), 16 rows (zero-padded) above
 template <typename T> void recombine_disp(const RecombParams<T> &p, cudaStream_t s) {
     constexpr bool dbl = sizeof(T) == 8;
-    if (p.nsite <= 4) launch_disp<T, 4, dbl ? 2 : 4>(p, s);
-    else if (p.nsite <= 8) launch_disp<T, 8, dbl ? 2 : 4>(p, s);
-    else launch_disp<T, 16, dbl ? 1 : 2>(p, s);
+    switch (p.nsite) {
+        case 1: launch_disp<T, 1, dbl ? 2 : 4, 2>(p, s); break;
+        case 2: launch_disp<T, 2, dbl ? 2 : 4, 2>(p, s); break;
+        case 3: launch_disp<T, 3, dbl ? 2 : 4, 2>(p, s); break;
+        case 4: launch_disp<T, 4, dbl ? 2 : 4, 2>(p, s); break;
+        case 5: launch_disp<T, 5, dbl ? 2 : 4, dbl ? 1 : 2>(p, s); break;
+        case 6: launch_disp<T, 6, 2, dbl ? 1 : 2>(p, s); break;
+        case 7: launch_disp<T, 7, 2, dbl ? 1 : 2>(p, s); break;
+        case 8: launch_disp<T, 8, 2, dbl ? 1 : 2>(p, s); break;
+        default: launch_disp<T, 16, dbl ? 1 : 2, 1>(p, s); break;
+    }
 }
 
 // <F(H)> of Eq. bragg_sf_disp: even orders of the k = 0 transforms averaged over supercells
