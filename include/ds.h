@@ -149,6 +149,19 @@ ds_status ds_model_upload_displacements(ds_model *model, const float *disp, int 
 ds_status ds_request_intensity(ds_model *model, const ds_qgrid *grid, const ds_opts *opts, void *out,
                                int out_is_device, void *stream, ds_result_info *info);
 
+/* I(Q) at npts arbitrary wavevectors (Section V B): hkl in r.l.u., [npts][3] doubles on the host
+ * or (hkl_is_device) the device; out: npts values of the precision's type, host or device.  Each
+ * point is resampled from I(G) on the supercell Bragg positions around it by Eq.
+ * intensity_convol_finite with W = W_sinc L (Eqs. weight_sinc, windowed_sinc, lanczos;
+ * opts->smoothing must be DS_SMOOTH_LANCZOS, with lanczos_m and lanczos_mprime): the sum runs
+ * over floor(Q_a) - M + 1 <= G_a <= floor(Q_a) + M, M = ceil(m m'/2), inside the strict window
+ * |Q_a - G_a| < m m'/2 (Q_a = n_a h_a).  I(G) is computed by the FFT method on the box of Bragg
+ * positions that covers every point's support.  The call returns when the values are written
+ * (it synchronises `stream`).  Errors: DS_ERR_ARG (smoothing, non-finite points), DS_ERR_ADMISSION
+ * (box larger than the budget), DS_ERR_UNSUPPORTED, the errors of ds_request_intensity. */
+ds_status ds_request_points(ds_model *model, const double *hkl, int64_t npts, int hkl_is_device, const ds_opts *opts,
+                            void *out, int out_is_device, void *stream, ds_result_info *info);
+
 /* Serving: queue a request (device `out`, kept valid until completion).  The call validates
  * the request, chooses the Taylor order (displacive, reading x_max back on the context's own
  * stream) and estimates its HBM footprint; a worker thread admits queued requests in arrival

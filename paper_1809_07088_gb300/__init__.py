@@ -161,6 +161,25 @@ class Model:
                                                      _stream_of(out, stream), C.byref(info)))
         return out, info.as_dict()
 
+    def intensity_points(self, hkl, out=None, stream=None, **opts):
+        """I(Q) at arbitrary points hkl [npts, 3] (r.l.u., float64; numpy or torch, host or CUDA)
+        by Lanczos resampling of I(G) (ds_request_points); smoothing defaults to Lanczos.
+        Returns (out, info dict); `out` may be a preallocated array or tensor of npts values."""
+        opts.setdefault("smoothing", DS_SMOOTH_LANCZOS)
+        o = make_opts(**opts)
+        dt = np.float64 if o.precision == DS_FP64 else np.float32
+        if not _is_torch(hkl):
+            hkl = np.ascontiguousarray(hkl, dtype=np.float64).reshape(-1, 3)
+        ph, hdev = _ptr(hkl, np.float64)
+        npts = int(hkl.shape[0]) if len(hkl.shape) == 2 else int(np.prod(hkl.shape)) // 3
+        if out is None:
+            out = np.empty(npts, dtype=dt)
+        po, odev = _ptr(out, dt)
+        info = ds_result_info()
+        self.ctx.check(self.lib.ds_request_points(self.h, ph, C.c_int64(npts), hdev, C.byref(o), po, odev,
+                                                  _stream_of(out, stream), C.byref(info)))
+        return out, info.as_dict()
+
     def backward(self, qgrid, dL_dI, grad=None, stream=None, **opts):
         """dL/du (displacive) or dL/dM (magnetic) for a given dL/dI on `qgrid`."""
         q = make_qgrid(*qgrid)

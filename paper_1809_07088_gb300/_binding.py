@@ -62,6 +62,8 @@ SIGNATURES = {
     "ds_model_upload_displacements": (st, [vp, vp, C.c_int, vp]),
     "ds_request_intensity": (st, [vp, C.POINTER(ds_qgrid), C.POINTER(ds_opts), vp, C.c_int, vp,
                                   C.POINTER(ds_result_info)]),
+    "ds_request_points": (st, [vp, vp, C.c_int64, C.c_int, C.POINTER(ds_opts), vp, C.c_int, vp,
+                               C.POINTER(ds_result_info)]),
     "ds_submit": (st, [vp, C.POINTER(ds_qgrid), C.POINTER(ds_opts), vp, C.POINTER(C.c_uint64)]),
     "ds_poll": (st, [vp, C.c_uint64, C.POINTER(ds_result_info)]),
     "ds_wait": (st, [vp, C.c_uint64, C.c_double, C.POINTER(ds_result_info)]),

@@ -1,0 +1,199 @@
+// Intensity at arbitrary wavevectors (Section V B): Lanczos resampling of I(G), Eq.
+// intensity_convol_finite with W = W_sinc L (Eqs. weight_sinc, windowed_sinc, lanczos), for Q
+// anywhere in reciprocal space (planes, lines, scattered points), not only on the grid of
+// supercell Bragg positions.
+//
+// I(G) is computed by the FFT method on the box of Bragg positions that covers the support of
+// every point (the commensurate path of api.cu), then one thread per point forms
+//     I(Q) = sum_G W(Q - G) I(G) / sum_G W(Q - G)
+// over floor(Q_a) - M + 1 <= G_a <= floor(Q_a) + M, M = ceil(m_eff), with the strict window
+// |Q_a - G_a| < m_eff.  W is a product of one-axis weights, so are its sums; the weights are
+// evaluated in FP64.
+#include <algorithm>
+#include <climits>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "api_internal.h"
+#include "noise.h"
+
+using namespace ds;
+
+namespace {
+
+constexpr double PI_D = 3.141592653589793238462643383279502884;
+
+// one-axis weight sinc(2 pi r_cut d) sinc(pi d / m_eff) inside the window, 0 outside
+__device__ __forceinline__ double axis_weight(double d, double rcut, double meff) {
+    if (!(fabs(d) < meff)) return 0.0;
+    if (d == 0.0) return 1.0;
+    const double x1 = 2.0 * rcut * d, x2 = d / meff;  // in units of pi
+    const double s1 = (x1 == 0.0) ? 1.0 : sinpi(x1) / (PI_D * x1);
+    return s1 * sinpi(x2) / (PI_D * x2);
+}
+
+// MAXT: taps per axis held in registers (2M <= MAXT)
+template <typename T, int MAXT>
+__global__ void k_lanczos_points(const T *__restrict__ vol, int b0, int b1, int b2, int c1, int c2,
+                                 const double *__restrict__ Q, long long npts, int M, double rcut, double meff,
+                                 T *__restrict__ out) {
+    const int ntap = 2 * M;
+    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < npts;
+         p += (long long)gridDim.x * blockDim.x) {
+        double w[3][MAXT];
+        double wsum[3];
+        int g0[3];
+        const int box[3] = {b0, b1, b2};
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const double q = Q[3 * p + a];
+            const double fq = floor(q);
+            g0[a] = (int)fq - M + 1 - box[a];  // first tap, relative to the box origin
+            wsum[a] = 0.0;
+#pragma unroll
+            for (int t = 0; t < MAXT; ++t) {
+                double v = 0.0;
+                if (t < ntap) v = axis_weight(q - (fq - M + 1 + t), rcut, meff);
+                w[a][t] = v;
+                wsum[a] += v;
+            }
+        }
+        T acc = T(0);
+#pragma unroll
+        for (int t0 = 0; t0 < MAXT; ++t0) {
+            if (t0 >= ntap || w[0][t0] == 0.0) continue;
+            T acc1 = T(0);
+#pragma unroll
+            for (int t1 = 0; t1 < MAXT; ++t1) {
+                if (t1 >= ntap || w[1][t1] == 0.0) continue;
+                const T *row = vol + ((size_t)(g0[0] + t0) * c1 + (g0[1] + t1)) * c2 + g0[2];
+                T acc2 = T(0);
+#pragma unroll
+                for (int t2 = 0; t2 < MAXT; ++t2)
+                    if (t2 < ntap) acc2 = fma((T)w[2][t2], row[t2], acc2);
+                acc1 = fma((T)w[1][t1], acc2, acc1);
+            }
+            acc = fma((T)w[0][t0], acc1, acc);
+        }
+        out[p] = acc / (T)(wsum[0] * wsum[1] * wsum[2]);
+    }
+}
+
+template <typename T>
+void launch_points(const T *vol, const int box[3], const int cnt[3], const double *dQ, long long npts, int M,
+                   double rcut, double meff, T *out, cudaStream_t s) {
+    const unsigned nb = (unsigned)std::max<long long>(1, std::min<long long>((npts + 127) / 128, 152 * 32));
+    if (2 * M <= 4)
+        k_lanczos_points<T, 4><<<nb, 128, 0, s>>>(vol, box[0], box[1], box[2], cnt[1], cnt[2], dQ, npts, M, rcut, meff, out);
+    else if (2 * M <= 8)
+        k_lanczos_points<T, 8><<<nb, 128, 0, s>>>(vol, box[0], box[1], box[2], cnt[1], cnt[2], dQ, npts, M, rcut, meff, out);
+    else if (2 * M <= 16)
+        k_lanczos_points<T, 16><<<nb, 128, 0, s>>>(vol, box[0], box[1], box[2], cnt[1], cnt[2], dQ, npts, M, rcut, meff, out);
+    else
+        k_lanczos_points<T, 64><<<nb, 128, 0, s>>>(vol, box[0], box[1], box[2], cnt[1], cnt[2], dQ, npts, M, rcut, meff, out);
+    count_launches(1);
+}
+
+template <typename T>
+ds_status run_points(ds_model *Mdl, const std::vector<double> &Qh, long long npts, const ds_opts *o, void *out,
+                     int out_dev, cudaStream_t st, ds_result_info *info) {
+    ds_ctx *ctx = Mdl->ctx;
+    const int m = o->lanczos_m, mp = o->lanczos_mprime;
+    const double rcut = (1.0 - 1.0 / m) / mp, meff = 0.5 * m * mp;
+    const int M = (int)std::ceil(meff);
+    // box of Bragg positions covering every point's support
+    long long lo[3], hi[3];
+    for (int a = 0; a < 3; ++a) {
+        lo[a] = LLONG_MAX;
+        hi[a] = LLONG_MIN;
+    }
+    for (long long p = 0; p < npts; ++p)
+        for (int a = 0; a < 3; ++a) {
+            const long long f = (long long)std::floor(Qh[3 * p + a]);
+            lo[a] = std::min(lo[a], f - M + 1);
+            hi[a] = std::max(hi[a], f + M);
+        }
+    ds_qgrid box;
+    int b[3], cnt[3];
+    size_t nvox = 1;
+    for (int a = 0; a < 3; ++a) {
+        if (hi[a] - lo[a] + 1 > (1 << 20) || std::llabs(lo[a]) > 100000000LL)
+            return ds_fail(ctx, DS_ERR_UNSUPPORTED, "points span too many Bragg positions along axis %d", a);
+        b[a] = (int)lo[a];
+        cnt[a] = (int)(hi[a] - lo[a] + 1);
+        box.h0[a] = (double)lo[a] / Mdl->n[a];
+        box.step[a] = 1.0 / Mdl->n[a];
+        box.count[a] = cnt[a];
+        nvox *= (size_t)cnt[a];
+    }
+    if (nvox * sizeof(T) > ctx->budget)
+        return ds_fail(ctx, DS_ERR_ADMISSION, "the box of Bragg positions under the points needs %zu bytes, budget %zu",
+                       nvox * sizeof(T), ctx->budget);
+    ds_opts ob = *o;
+    ob.smoothing = DS_SMOOTH_NONE;
+    Scratch ws(st);
+    T *vol = (T *)ws.get(sizeof(T) * nvox);
+    double *dQ = (double *)ws.get(sizeof(double) * 3 * npts);
+    T *dout = out_dev ? (T *)out : (T *)ws.get(sizeof(T) * npts);
+    if (ws.failed) return ds_fail(ctx, DS_ERR_OOM, "device allocation failed (points)");
+    ds_status rc = plan_and_run<T>(Mdl, &box, &ob, vol, st, ws, info, nullptr);
+    if (rc != DS_OK) return rc;
+    if (cudaMemcpyAsync(dQ, Qh.data(), sizeof(double) * 3 * npts, cudaMemcpyHostToDevice, st) != cudaSuccess)
+        return ds_fail(ctx, DS_ERR_CUDA, "copy of the points failed");
+    {
+        ProfScope ps(ctx, "lanczos_points", st);
+        launch_points<T>(vol, b, cnt, dQ, npts, M, rcut, meff, dout, st);
+    }
+    if (!out_dev && cudaMemcpyAsync(out, dout, sizeof(T) * npts, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+        return ds_fail(ctx, DS_ERR_CUDA, "copy of the intensities to the host failed");
+    ws.release();
+    // the host copy of the points must outlive the copy queued above; host outputs are waited for
+    if (cudaStreamSynchronize(st) != cudaSuccess)
+        return ds_fail(ctx, DS_ERR_CUDA, "stream synchronisation failed: %s", cudaGetErrorString(cudaGetLastError()));
+    if (info) info->nvox = npts;
+    return DS_OK;
+}
+
+}  // namespace
+
+extern "C" ds_status ds_request_points(ds_model *Mdl, const double *hkl, int64_t npts, int hkl_is_device,
+                                       const ds_opts *o, void *out, int out_is_device, void *stream,
+                                       ds_result_info *info) {
+    if (!Mdl) return DS_ERR_ARG;
+    ds_ctx *ctx = Mdl->ctx;
+    if (!o) return ds_fail(ctx, DS_ERR_ARG, "null options");
+    if (npts < 0) return ds_fail(ctx, DS_ERR_ARG, "negative point count");
+    if (npts > 0 && (!hkl || !out)) return ds_fail(ctx, DS_ERR_ARG, "null points or output");
+    if (o->smoothing != DS_SMOOTH_LANCZOS)
+        return ds_fail(ctx, DS_ERR_ARG, "points off the Bragg grid need smoothing = DS_SMOOTH_LANCZOS");
+    if (!Mdl->has_cells) return ds_fail(ctx, DS_ERR_STATE, "model incomplete");
+    if (info) memset(info, 0, sizeof(*info));
+    if (npts == 0) return DS_OK;
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return ds_fail(ctx, DS_ERR_CUDA, "cudaSetDevice");
+    cudaStream_t st = (cudaStream_t)stream;
+    std::vector<double> Qh((size_t)npts * 3);
+    if (hkl_is_device) {
+        if (cudaMemcpy(Qh.data(), hkl, sizeof(double) * 3 * npts, cudaMemcpyDeviceToHost) != cudaSuccess)
+            return ds_fail(ctx, DS_ERR_CUDA, "copy of the points to the host failed");
+    } else {
+        std::copy(hkl, hkl + 3 * npts, Qh.begin());
+    }
+    for (long long p = 0; p < npts; ++p)
+        for (int a = 0; a < 3; ++a) {
+            const double q = Qh[3 * p + a] * Mdl->n[a];  // supercell-index units, Q_a = n_a h_a
+            if (!std::isfinite(q)) return ds_fail(ctx, DS_ERR_ARG, "point %lld is not finite", p);
+            Qh[3 * p + a] = q;
+        }
+    // options and model state, checked on a one-voxel grid at the first point's floor
+    ds_qgrid probe;
+    for (int a = 0; a < 3; ++a) {
+        probe.h0[a] = std::floor(Qh[a]) / Mdl->n[a];
+        probe.step[a] = 1.0 / Mdl->n[a];
+        probe.count[a] = 1;
+    }
+    ds_status rc = check_request(Mdl, &probe, o);
+    if (rc != DS_OK) return rc;
+    if (o->precision == DS_FP64) return run_points<double>(Mdl, Qh, npts, o, out, out_is_device, st, info);
+    return run_points<float>(Mdl, Qh, npts, o, out, out_is_device, st, info);
+}

@@ -165,6 +165,74 @@ def test_lanczos_commensurate(ctx, m_, mp):
         assert rel_err_of_peak(got, want) < TOL[tag]
 
 
+@pytest.mark.parametrize("prec,tag", PREC)
+@pytest.mark.parametrize("m_,mp", [(2, 2), (3, 2), (2, 4)])
+def test_points_arbitrary_occupancy(ctx, prec, tag, m_, mp):
+    """Lanczos resampling at arbitrary wavevectors (Section V B, Eq. intensity_convol_finite with
+    floor bounds and the strict window): random points, points on Bragg positions and negative
+    coordinates, against the oracle's literal finite sum over I(G) of the oracle's FFT method."""
+    m = syn.small_case(syn.OCC, cells=(6, 5, 4), nsite=3, nmodels=2, seed=131)
+    lm = to_library(ctx, m)
+    rng = np.random.default_rng(7)
+    hkl = np.concatenate([rng.uniform(-1.3, 1.3, (200, 3)),
+                          np.array([[0.0, 0.0, 0.0], [1 / 6, -2 / 5, 0.25], [-1.0, 0.5, 1.0]])])
+    got, info = lm.intensity_points(hkl, disorder=0, mode=1, precision=prec, lanczos_m=m_, lanczos_mprime=mp)
+    assert info["nvox"] == hkl.shape[0]
+    Q = hkl * np.array(m.cells)
+    want = noise.lanczos_resample(lambda G: core.occupancy_intensity_fft(m, G, 1), Q, m_, mp)
+    assert rel_err_of_peak(got, want) < TOL[tag]
+
+
+@pytest.mark.parametrize("prec,tag", PREC)
+def test_points_hhl_plane_magnetic(ctx, prec, tag):
+    """An (h h l) plane off the Bragg grid (the paper's plane geometry, Section IV) for the
+    magnetic intensity with the <j0> form factor, device points and device output."""
+    import torch
+    m = syn.pyrochlore_occ_mag(cells=(4, 4, 4), nmodels=2, hmax=1.0, seed=12)
+    mm = syn.magnetic_view(m)
+    lm = to_library(ctx, mm)
+    u, v = np.meshgrid(np.linspace(-1.55, 1.45, 23), np.linspace(-2.1, 1.9, 21), indexing="ij")
+    hkl = np.stack([u.ravel(), u.ravel(), v.ravel()], axis=1)
+    dt = torch.float64 if prec == 0 else torch.float32
+    out = torch.empty(hkl.shape[0], dtype=dt, device="cuda")
+    lm.intensity_points(torch.from_numpy(hkl).cuda(), out=out, disorder=1, mode=0, precision=prec, lanczos_m=2,
+                        lanczos_mprime=2)
+    torch.cuda.synchronize()
+    want = noise.lanczos_resample(lambda G: core.magnetic_intensity_fft(mm, G, 0), hkl * 4.0, 2, 2)
+    assert rel_err_of_peak(out.cpu().numpy(), want) < TOL[tag]
+
+
+@pytest.mark.parametrize("prec,tag", PREC)
+def test_points_displacive_and_grid_consistency(ctx, prec, tag):
+    """Displacive points (fixed Taylor order) against the oracle; points placed exactly on Bragg
+    positions equal the commensurate Lanczos volume of ds_request_intensity."""
+    m = syn.small_case(syn.DISP, cells=(4, 6, 5), nsite=3, nmodels=2, seed=132, sigma=0.08)
+    lm = to_library(ctx, m)
+    rng = np.random.default_rng(8)
+    hkl = rng.uniform(-0.9, 0.9, (120, 3))
+    opts = dict(disorder=2, mode=1, precision=prec, taylor_order=6, lanczos_m=2, lanczos_mprime=2)
+    got, _ = lm.intensity_points(hkl, **opts)
+    want = noise.lanczos_resample(lambda G: core.displacive_intensity_fft(m, G, 1, P=6), hkl * np.array(m.cells), 2, 2)
+    assert rel_err_of_peak(got, want) < TOL[tag]
+    vol, _ = lm.intensity(qgrid_tuple(m.qgrid), smoothing=1, **opts)
+    G = _G(m)
+    pick = np.random.default_rng(9).choice(G.shape[0], 50, replace=False)
+    on_grid, _ = lm.intensity_points(G[pick] / np.array(m.cells), **opts)
+    assert rel_err_of_peak(on_grid, vol.reshape(-1)[pick]) < TOL[tag]
+
+
+def test_points_errors(ctx):
+    import paper_1809_07088_gb300 as ds
+    m = syn.small_case(syn.OCC, cells=(3, 3, 3), nsite=1, nmodels=1, seed=133)
+    lm = to_library(ctx, m)
+    with pytest.raises(ds.DSError):
+        lm.intensity_points(np.zeros((3, 3)), disorder=0, smoothing=0)
+    with pytest.raises(ds.DSError):
+        lm.intensity_points(np.array([[np.nan, 0.0, 0.0]]), disorder=0)
+    out, info = lm.intensity_points(np.zeros((0, 3)), disorder=0)
+    assert out.shape == (0,) and info["nvox"] == 0
+
+
 def test_device_output_on_torch_stream(ctx):
     import torch
     m = syn.small_case(syn.OCC, cells=(6, 5, 4), nsite=3, nmodels=1, seed=107)
