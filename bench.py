@@ -414,6 +414,9 @@ def run_ours(args):
     lm_n.close()
     lm_m.close()
     ctx.close()
+    rows = None
+    if rank == 0 and not args.no_rows:
+        rows = run_rows(dev)
     if args.serving > 0:
         serving = run_serving(args.serving, nreq_fp64=min(32, args.serving))
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -424,10 +427,129 @@ def run_ours(args):
             "max_rel_err_vs_fp64": max(errs), "fp64_plain": {"ms_per_step": ms64, "value": ws * vox_step / (ms64 / 1e3)},
             "e2e": e2e, "roofline": roofline, "stages": stages, "gpu_launches": int(prof.get("launches", 0)),
             "wall_ms_per_step": 1e3 * t_wall / args.steps, "clocks": clk, "cpu_baseline": cpu,
-            "serving": serving}
+            "serving": serving, "rows": rows}
     if rank == 0:
         print(json.dumps(line))
     return 0
+
+
+# ----------------------------------------------------------------------------------------------
+# the other rows of the path, each timed on its own workload (device events, warm)
+# ----------------------------------------------------------------------------------------------
+
+def run_rows(dev):
+    """One measurement per remaining step of the path: the Taylor (displacive) recombination and
+    its adjoint on the fcc 32^3 / 321^3 case, Lanczos resampling on a 1025^3 volume, exact sub-box
+    averaging and arbitrary-wavevector resampling on an (h h l) plane of 401 x 401 points."""
+    import ctypes
+    import numpy as np
+    import torch
+    import paper_1809_07088_gb300 as ds
+    import synthetic as syn
+
+    peaks, _ = measured_peaks()
+    hbm = float(peaks["hbm_gbs"])
+    alu = 78.2  # TFLOP/s, FP32 FMA-chain measurement on this GPU model
+    ctx = ds.Context(dev.index or 0)
+    buf = ctypes.create_string_buffer(1 << 16)
+
+    def timed(fn, reps=3):
+        fn()
+        torch.cuda.synchronize(dev)
+        ctx.lib.ds_profile_report(ctx.h, buf, len(buf))
+        ctx.lib.ds_profile_enable(ctx.h, 1)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(reps):
+            fn()
+        b.record()
+        torch.cuda.synchronize(dev)
+        ctx.lib.ds_profile_enable(ctx.h, 0)
+        ctx.check(ctx.lib.ds_profile_report(ctx.h, buf, len(buf)))
+        st = json.loads(buf.value.decode())["stages"]
+        return a.elapsed_time(b) / reps, {k: v["ms"] / max(1, v["count"]) for k, v in st.items()}
+
+    rows = {}
+    # Taylor recombination (S1-S5 displacive) and adjoint (S7): fcc 32^3, 321^3 voxels, eps 1e-8
+    m = syn.displacive_fcc(cells=(32, 32, 32), sigma=0.1, seed=5)
+    m.qgrid = syn.symmetric_qgrid(5.0, m.cells)
+    lm = ds.Model(ctx, m.lattice, m.sites, m.cells, 1, m.scat_len, m.ff_kind, m.ff_coef)
+    lm.upload_displacements(np.ascontiguousarray(m.disp))
+    q = (m.qgrid.h0, m.qgrid.step, m.qgrid.count)
+    out = torch.empty(m.qgrid.count, dtype=torch.float32, device=dev)
+    for zonal in (0, 1):
+        o = dict(disorder=ds.DS_DISP, mode=ds.DS_TOTAL, precision=ds.DS_FP32, taylor_order=-1, taylor_eps=1e-8,
+                 taylor_zonal=zonal)
+        _, info = lm.intensity(q, out=out, **o)
+        ms, st = timed(lambda: lm.intensity(q, out=out, **o))
+        T = info["n_monomials"]
+        rec = st.get("recombine_disp", float("nan"))
+        flops = m.qgrid.nvox * m.nsite * T * 4.0 + m.qgrid.nvox * T   # one-order bound for both
+        rows["taylor_fcc32_zonal%d" % zonal] = {
+            "workload": "fcc 32^3 cells, u ~ N(0, 0.1^2), |hkl| <= 5 step 1/32 (321^3 voxels), FP32, eps 1e-8",
+            "taylor_order": info["taylor_order"], "monomials": T, "ms": ms, "stages_ms": st,
+            "voxels_per_s": m.qgrid.nvox / (ms / 1e3),
+            "roofline": {"bound": "alu", "achieved": flops / (rec / 1e3) / 1e12 if zonal == 0 else None,
+                         "peak": alu, "unit": "TFLOP/s",
+                         "frac": flops / (rec / 1e3) / 1e12 / alu if zonal == 0 else None,
+                         "note": "nsite x T complex x real multiply-adds + T coefficient multiplies per voxel"}}
+    dL = torch.ones(m.qgrid.count, dtype=torch.float32, device=dev)
+    g = torch.empty((1, m.nsite) + tuple(m.cells) + (3,), dtype=torch.float32, device=dev)
+    ms, st = timed(lambda: lm.backward(q, dL, grad=g, disorder=ds.DS_DISP, mode=ds.DS_TOTAL, precision=ds.DS_FP32,
+                                       taylor_order=-1, taylor_eps=1e-8), reps=2)
+    rows["adjoint_fcc32"] = {"workload": "dchi2/du of the fcc 32^3 case above, FP32", "ms": ms, "stages_ms": st}
+    lm.close()
+    del out, dL, g
+
+    # Lanczos resampling (S6a): 1025^3 voxels (|hkl| <= 8 step 1/64), m = 2, m' = 8, occupancy
+    n = 64
+    mo = syn.Model(lattice=(4.0, 4.0, 4.0, 90.0, 90.0, 90.0), sites=np.array([[0.0, 0.0, 0.0]]),
+                   scat_len=np.ones(1), ff_kind=np.zeros(1, dtype=np.int32), ff_coef=np.zeros((1, 9)),
+                   cells=(n, n, n), nmodels=1)
+    mo.occ = (np.random.default_rng(3).random((1, 1, n, n, n)) < 0.5).astype(np.uint8)
+    lo = ds.Model(ctx, mo.lattice, mo.sites, mo.cells, 1, mo.scat_len, mo.ff_kind, mo.ff_coef)
+    lo.upload_occupancy(np.ascontiguousarray(mo.occ))
+    qg = syn.symmetric_qgrid(8.0, mo.cells)
+    q = (qg.h0, qg.step, qg.count)
+    out = torch.empty(qg.count, dtype=torch.float32, device=dev)
+    ms, st = timed(lambda: lo.intensity(q, out=out, disorder=ds.DS_OCC, mode=ds.DS_DIFFUSE, precision=ds.DS_FP32,
+                                        smoothing=ds.DS_SMOOTH_LANCZOS, lanczos_m=2, lanczos_mprime=8), reps=2)
+    lz = st.get("lanczos", float("nan"))
+    h = 7
+    ext = [c + 2 * h for c in qg.count]
+    c = qg.count
+    lz_bytes = 4.0 * (ext[0] * ext[1] * ext[2] + 2 * ext[0] * ext[1] * c[2] + 2 * ext[0] * c[1] * c[2]
+                      + c[0] * c[1] * c[2])
+    rows["lanczos_1025cubed"] = {
+        "workload": "occupancy 64^3 cells, |hkl| <= 8 step 1/64 (1025^3 voxels), Lanczos m = 2, m' = 8, FP32",
+        "ms": ms, "stages_ms": st,
+        "roofline": {"bound": "hbm", "achieved": lz_bytes / (lz / 1e3) / 1e9, "peak": hbm, "unit": "GB/s",
+                     "frac": lz_bytes / (lz / 1e3) / 1e9 / hbm,
+                     "note": "three one-axis passes, each reading and writing its volume once (4 B per voxel)"}}
+    lo.close()
+    del out
+
+    # exact sub-box averaging (S6b) and arbitrary wavevectors (S6a'): the pyrochlore workload
+    mp = syn.pyrochlore_occ_mag()
+    lp = ds.Model(ctx, mp.lattice, mp.sites, mp.cells, 1, mp.scat_len, mp.ff_kind, mp.ff_coef)
+    lp.upload_occupancy(np.ascontiguousarray(mp.occ))
+    q = (mp.qgrid.h0, mp.qgrid.step, mp.qgrid.count)
+    out = torch.empty(mp.qgrid.count, dtype=torch.float32, device=dev)
+    ms, st = timed(lambda: lp.intensity(q, out=out, disorder=ds.DS_OCC, mode=ds.DS_DIFFUSE, precision=ds.DS_FP32,
+                                        smoothing=ds.DS_SMOOTH_SUBBOX, subbox_n=5), reps=2)
+    rows["subbox_pyrochlore"] = {"workload": "pyrochlore occupancy 20^3, 241^3 voxels, n_sb = 5, FP32", "ms": ms,
+                                 "stages_ms": st, "voxels_per_s": mp.qgrid.nvox / (ms / 1e3)}
+    u, v = np.meshgrid(np.linspace(-6.0, 6.0, 401), np.linspace(-6.0 * 2 ** 0.5, 6.0 * 2 ** 0.5, 401), indexing="ij")
+    hkl = torch.from_numpy(np.stack([u.ravel(), u.ravel(), v.ravel()], axis=1)).to(dev)
+    pts = torch.empty(hkl.shape[0], dtype=torch.float32, device=dev)
+    ms, st = timed(lambda: lp.intensity_points(hkl, out=pts, disorder=ds.DS_OCC, mode=ds.DS_DIFFUSE,
+                                               precision=ds.DS_FP32, lanczos_m=2, lanczos_mprime=2), reps=2)
+    rows["points_hhl_plane"] = {"workload": "(h h l) plane 401 x 401 points, |h| <= 6, |l| <= 6 sqrt 2, pyrochlore "
+                                            "occupancy 20^3, Lanczos m = 2, FP32 (the paper's plane geometry)",
+                                "ms": ms, "stages_ms": st, "points_per_s": hkl.shape[0] / (ms / 1e3)}
+    lp.close()
+    ctx.close()
+    return rows
 
 
 # ----------------------------------------------------------------------------------------------
@@ -563,6 +685,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serving", type=int, default=128, help="requests in the serving stream (0 = skip)")
+    ap.add_argument("--no-rows", action="store_true", help="skip the per-row measurements")
     ap.add_argument("--streams", type=int, default=2, choices=[1, 2],
                     help="2: the two volumes of a step on two streams (their kernels overlap)")
     args = ap.parse_args()
