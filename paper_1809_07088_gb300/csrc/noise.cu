@@ -7,7 +7,9 @@
 // normalised to unit sum (the 8 r_cut^3 prefactor and the denominator of Eq.
 // intensity_convol_finite both cancel in the normalisation).  r_cut = (1 - 1/m)/m' and
 // m_eff = m m' / 2 (m' = 2 is the plain window; larger m' reaches zero at 1/m').  Each pass
-// shrinks the volume by the halo h = ceil(m_eff) - 1 on both sides of its axis.
+// shrinks the volume by the halo h = ceil(m_eff) - 1 on both sides of its axis.  Stencils of up
+// to 17 taps run as sliding windows (each input read about once per pass: HBM bound); wider
+// ones with one thread per output.
 #include <algorithm>
 
 #include "internal.h"
@@ -61,11 +63,133 @@ int lanczos_halo(int m, int mprime) {
     return (int)ceil(meff) - 1;
 }
 
+// normalised one-axis stencil of (2h+1) taps, FP64 on the host
+static void lanczos_taps(int h, double rcut, double meff, double *w) {
+    const double pi = 3.141592653589793238462643383279502884;
+    double sum = 0.0;
+    for (int i = 0; i <= 2 * h; ++i) {
+        const double d = (double)(i - h);
+        double v = 0.0;
+        if (fabs(d) < meff) {
+            v = 1.0;
+            if (d != 0.0) {
+                const double x1 = pi * 2.0 * rcut * d, x2 = pi * d / meff;
+                v = (sin(x1) / x1) * (sin(x2) / x2);
+            }
+        }
+        w[i] = v;
+        sum += v;
+    }
+    for (int i = 0; i <= 2 * h; ++i) w[i] /= sum;
+}
+
+template <typename T> struct Taps {
+    T w[64];
+};
+
+// Pass along the middle axis of a volume viewed as [A][B][C] (C contiguous): out[a][b][c] =
+// sum_t w_t in[a][b + t][c], b < B - 2h.  A thread owns one (a, c) column and a run of L
+// outputs along B, keeping the last NT inputs in registers (a sliding window), so each input is
+// read about (L + NT - 1) / L times; consecutive threads take consecutive c (coalesced).
+template <typename T, int NT>
+__global__ void __launch_bounds__(256) k_lanczos_mid(const T *__restrict__ in, T *__restrict__ out, int A, int B, int C,
+                                                     int L, const __grid_constant__ Taps<T> tp) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    const int Bo = B - (NT - 1);
+    const int nrun = (Bo + L - 1) / L;
+    const int a = blockIdx.y / nrun, run = blockIdx.y - a * nrun;
+    if (c >= C || a >= A) return;
+    const int b0 = run * L, b1 = min(Bo, b0 + L);
+    const T *src = in + ((size_t)a * B + b0) * C + c;
+    T *dst = out + ((size_t)a * Bo + b0) * C + c;
+    T ring[NT];
+#pragma unroll
+    for (int t = 0; t < NT - 1; ++t) ring[t] = src[(size_t)t * C];
+    for (int b = b0; b < b1; ++b) {
+        ring[NT - 1] = src[(size_t)(b - b0 + NT - 1) * C];
+        T acc = T(0);
+#pragma unroll
+        for (int t = 0; t < NT; ++t) acc = fma(tp.w[t], ring[t], acc);
+        dst[(size_t)(b - b0) * C] = acc;
+#pragma unroll
+        for (int t = 0; t < NT - 1; ++t) ring[t] = ring[t + 1];
+    }
+}
+
+// Pass along the contiguous axis of [R][C]: a block stages a row segment and its halo in shared
+// memory (coalesced), then each thread forms outputs from the staged values.
+template <typename T, int NT>
+__global__ void __launch_bounds__(256) k_lanczos_row(const T *__restrict__ in, T *__restrict__ out, int C, int SEG,
+                                                     const __grid_constant__ Taps<T> tp) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *seg = (T *)smem_raw;
+    const int Co = C - (NT - 1);
+    const int nseg = (Co + SEG - 1) / SEG;
+    const size_t r = blockIdx.x / nseg;
+    const int s0 = (int)(blockIdx.x - r * nseg) * SEG;
+    const int n = min(SEG, Co - s0);
+    const T *src = in + r * C + s0;
+    for (int i = threadIdx.x; i < n + NT - 1; i += blockDim.x) seg[i] = src[i];
+    __syncthreads();
+    T *dst = out + r * Co + s0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        T acc = T(0);
+#pragma unroll
+        for (int t = 0; t < NT; ++t) acc = fma(tp.w[t], seg[i + t], acc);
+        dst[i] = acc;
+    }
+}
+
+template <typename T, int NT>
+static void sliding_passes(const T *ext, T *tmp1, T *tmp2, T *out, int d[3], const double *wd, cudaStream_t s) {
+    Taps<T> tp;
+    for (int i = 0; i < 64; ++i) tp.w[i] = i < NT ? (T)wd[i] : T(0);
+    const int h = (NT - 1) / 2;
+    // axis 2 (contiguous): rows of d2, segments of up to 2048 outputs
+    {
+        const size_t R = (size_t)d[0] * d[1];
+        const int Co = d[2] - 2 * h, SEG = std::min(Co, 2048);
+        const size_t nb = R * (size_t)((Co + SEG - 1) / SEG);
+        k_lanczos_row<T, NT><<<(unsigned)nb, 256, (SEG + NT - 1) * sizeof(T), s>>>(ext, tmp1, d[2], SEG, tp);
+        d[2] = Co;
+    }
+    // axis 1: [d0][d1][d2], then axis 0: [1][d0][d1 d2]; runs of L outputs per thread
+    auto mid = [&](const T *a, T *b, int A, int B, int C) {
+        // runs of at least 64 outputs, longer when A x runs would exceed the grid's y limit
+        const int Bo = B - 2 * h;
+        const int L = std::max(64, (int)(((long long)Bo * A + 65534) / 65535));
+        const int nrun = (Bo + L - 1) / L;
+        dim3 grid((unsigned)((C + 255) / 256), (unsigned)(A * nrun));
+        k_lanczos_mid<T, NT><<<grid, 256, 0, s>>>(a, b, A, B, C, L, tp);
+    };
+    mid(tmp1, tmp2, d[0], d[1], d[2]);
+    d[1] -= 2 * h;
+    mid(tmp2, out, 1, d[0], d[1] * d[2]);
+    d[0] -= 2 * h;
+    count_launches(3);
+}
+
 template <typename T>
 void lanczos_resample(const T *ext, T *tmp1, T *tmp2, T *out, const int cnt[3], int m, int mprime, cudaStream_t s) {
     const int h = lanczos_halo(m, mprime);
     const double rcut = (1.0 - 1.0 / m) / mprime, meff = 0.5 * m * mprime;
     int d[3] = {cnt[0] + 2 * h, cnt[1] + 2 * h, cnt[2] + 2 * h};
+    double wd[64];
+    lanczos_taps(h, rcut, meff, wd);
+    // the strided passes put (outer index x runs) on the grid's y axis
+    const bool fits = (long long)d[0] <= 65535;
+    switch (fits ? 2 * h + 1 : 0) {
+        case 3: sliding_passes<T, 3>(ext, tmp1, tmp2, out, d, wd, s); return;
+        case 5: sliding_passes<T, 5>(ext, tmp1, tmp2, out, d, wd, s); return;
+        case 7: sliding_passes<T, 7>(ext, tmp1, tmp2, out, d, wd, s); return;
+        case 9: sliding_passes<T, 9>(ext, tmp1, tmp2, out, d, wd, s); return;
+        case 11: sliding_passes<T, 11>(ext, tmp1, tmp2, out, d, wd, s); return;
+        case 13: sliding_passes<T, 13>(ext, tmp1, tmp2, out, d, wd, s); return;
+        case 15: sliding_passes<T, 15>(ext, tmp1, tmp2, out, d, wd, s); return;
+        case 17: sliding_passes<T, 17>(ext, tmp1, tmp2, out, d, wd, s); return;
+        default: break;
+    }
+    // wider stencils: one thread per output voxel
     const size_t sm = (2 * h + 1) * sizeof(T);
     auto launch = [&](const T *a, T *b, int axis) {
         size_t tot = (size_t)d[0] * d[1] * d[2];
