@@ -720,6 +720,16 @@ size_t request_footprint(const ds_model *M, const ds_qgrid *q, const ds_opts *o,
     return bytes;
 }
 
+// residue classes of zones along each axis (the period of exp(2 pi i H_a r_mu,a), or every zone its
+// own class); dres stays 0 unless the classes are at most half as many as the zones
+bool residue_classes(const ds_model *M, const GridMap &gm, int dres[3]) {
+    int d[3];
+    for (int a = 0; a < 3; ++a) d[a] = (M->period[a] > 0 && M->period[a] < gm.nH[a]) ? M->period[a] : gm.nH[a];
+    if (2LL * d[0] * d[1] * d[2] > (long long)gm.nH[0] * gm.nH[1] * gm.nH[2]) return false;
+    for (int a = 0; a < 3; ++a) dres[a] = d[a];
+    return true;
+}
+
 // site phase tables exp(2 pi i k_a r_a / n_a) and exp(2 pi i H_a r_a) of a grid, cached per model
 // (at most 256 grids; beyond that they are rebuilt in request scratch); a stream that did not
 // build them waits for the building stream's kernel
@@ -795,14 +805,7 @@ ds_status plan_and_run(ds_model *M, const ds_qgrid *q, const ds_opts *o, T *d_ou
     if constexpr (sizeof(T) == 4) p.ff = M->ff32;
     else p.ff = M->ff64;
     p.grp = M->groups;
-    if (o->disorder != DS_DISP) {
-        // residue classes of zones: used when they are at most half as many as the zones
-        int dres[3];
-        for (int a = 0; a < 3; ++a)
-            dres[a] = (M->period[a] > 0 && M->period[a] < gm.nH[a]) ? M->period[a] : gm.nH[a];
-        if (2LL * dres[0] * dres[1] * dres[2] <= (long long)gm.nH[0] * gm.nH[1] * gm.nH[2])
-            for (int a = 0; a < 3; ++a) p.dres[a] = dres[a];
-    }
+    if (o->disorder != DS_DISP) residue_classes(M, gm, p.dres);
     set_reciprocal(p, M->recip, g.n);
     const double N = (double)nsite * g.ncell;
     p.norm = (T)(1.0 / (nmod * N));

@@ -154,6 +154,7 @@ ds_status enqueue_request(ds_model *M, const ds_qgrid *q, const ds_opts *o, T *d
 ds_status resolve_taylor_order(ds_model *M, const ds_qgrid *q, const ds_opts *o, cudaStream_t st, Scratch &ws, int *P,
                                double *xmax, double *umax = nullptr);
 size_t request_footprint(const ds_model *M, const ds_qgrid *q, const ds_opts *o, int P);
+bool residue_classes(const ds_model *M, const ds::GridMap &gm, int dres[3]);
 // sub-box averaging (subbox.cu)
 template <typename T>
 ds_status subbox_run(ds_model *M, const ds_qgrid *q, const ds_opts *o, T *d_out, cudaStream_t st, Scratch &ws,

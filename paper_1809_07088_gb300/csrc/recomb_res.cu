@@ -13,7 +13,7 @@
 // identical up to rounding.  The library picks this kernel when the classes are at least twice
 // fewer than the zones; an axis without such a period counts each zone as its own class.
 //
-// Work split: a thread owns one k; a CTA owns 256 consecutive k, one class (rho1, rho2) of zone
+// Work split: a thread owns one k; a CTA owns 128 consecutive k, one class (rho1, rho2) of zone
 // columns and a share of the rho3 classes, formed a few at a time in one pass over the sites
 // (the per-site transforms are streamed from the L2-resident spectra, not kept in registers).
 // Every voxel is written by exactly one thread.

@@ -165,6 +165,143 @@ __global__ void __launch_bounds__(256) k_subbox_recomb(const __grid_constant__ R
     p.out[v] = p.norm * acc;
 }
 
+// Residue-class contraction (sites on special positions, one form-factor class): with
+// P_mu = f exp(iH.r_mu) exp(ik.r_mu), the pair sum of a voxel is
+//     f^2 sum_{p<=q} (2 - delta_pq) Re[exp(iH.(r_mu - r_nu)) D_pq(k)] proj_ab(Q),
+//     D_pq(k) = exp(ik.(r_mu - r_nu)) S_pq(k),
+// and exp(iH.(r_mu - r_nu)) depends on H only through its residue class (see recomb_res.cu).  A
+// thread owns one k and a class (rho1, rho2); it forms the class sums C_ab once per rho3 (for
+// spins six sums, the off-diagonal ones holding both orders of a, b) and each voxel then costs
+// f^2 (tr C - Q.C.Q / |Q|^2).
+template <typename T, int NC, int D3>
+__global__ void __launch_bounds__(128, 4)
+    k_subbox_res(const __grid_constant__ RecombParams<T> p, const c_t<T> *S, int s3) {
+    using C = c_t<T>;
+    constexpr int NSYM = NC == 3 ? 6 : 1;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int nsite = p.nsite, nf = nsite * NC;
+    const int n1 = p.g.n[0], n2 = p.g.n[1], n3 = p.g.n[2];
+    const int d1 = p.dres[0], d2 = p.dres[1], d3 = p.dres[2];
+    const int part = blockIdx.y % s3;
+    const int r12 = blockIdx.y / s3;
+    const int rho1 = r12 / d2, rho2 = r12 - rho1 * d2;
+    C *P123 = (C *)smem_raw;                                  // [d3][nsite]
+    C *ek = P123 + (size_t)d3 * nsite;                        // [nsite][128]: exp(ik.r_mu)
+    for (int idx = threadIdx.x; idx < d3 * nsite; idx += blockDim.x) {
+        const int r3 = idx / nsite, s = idx - r3 * nsite;
+        const C *t = p.phH + (size_t)s * 3 * p.nHmax;        // sites in input order
+        P123[idx] = cmul(cmul(t[rho1], t[p.nHmax + rho2]), t[2 * p.nHmax + r3]);
+    }
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool kvalid = k < p.g.ncell;
+    const int kq = kvalid ? k : 0;
+    const int k3 = kq % n3, k2 = (kq / n3) % n2, k1 = kq / (n3 * n2);
+    for (int s = 0; s < nsite; ++s) {
+        const C *t = p.phk + (size_t)s * 3 * p.nmax;
+        ek[(size_t)s * blockDim.x + threadIdx.x] = cmul(cmul(t[k1], t[p.nmax + k2]), t[2 * p.nmax + k3]);
+    }
+    __syncthreads();
+    if (!kvalid) return;
+    int conj;
+    const int kidx = half_index(p.g, k1, k2, k3, conj);
+    const GridMap &gm = p.gm;
+    const int g01 = gm.g0[0], g02 = gm.g0[1], g03 = gm.g0[2], cnt1 = gm.cnt[0], cnt2 = gm.cnt[1], cnt3 = gm.cnt[2];
+    const int G1b = n1 * gm.Hmin[0] + k1, G2b = n2 * gm.Hmin[1] + k2, G3b = n3 * gm.Hmin[2] + k3;
+    // zones h3 whose voxel G3 = G3b + n3 h3 lies in [g03, g03 + cnt3)
+    auto fdiv = [](int a, int b) { return a >= 0 ? a / b : -((-a + b - 1) / b); };
+    const int lo3 = max(-fdiv(-(g03 - G3b), n3), 0);
+    const int h3hi = min(fdiv(g03 + cnt3 - 1 - G3b, n3), gm.nH[2] - 1);
+    T qs[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) qs[i] = p.qstep[i];
+    const T norm = p.norm;
+    const int stride = n3 * d3;
+    const int nchunk = (d3 + D3 - 1) / D3;
+    const int lo3_mod = lo3 % d3;
+
+    for (int ch = part; ch < nchunk; ch += s3) {
+        const int r0 = ch * D3;
+        T acc[D3][NSYM];
+#pragma unroll
+        for (int r = 0; r < D3; ++r)
+#pragma unroll
+            for (int c = 0; c < NSYM; ++c) acc[r][c] = T(0);
+        for (int mu = 0; mu < nsite; ++mu) {
+            const C emu = ek[(size_t)mu * blockDim.x + threadIdx.x];
+            for (int nu = mu; nu < nsite; ++nu) {
+                const C ekk = cmulc(emu, ek[(size_t)nu * blockDim.x + threadIdx.x]);  // e^{ik.(r_mu - r_nu)}
+                C E[D3];
+#pragma unroll
+                for (int r = 0; r < D3; ++r)
+                    E[r] = (r0 + r < d3) ? cmulc(P123[(size_t)(r0 + r) * nsite + mu], P123[(size_t)(r0 + r) * nsite + nu])
+                                         : mk<T>(T(0), T(0));
+#pragma unroll
+                for (int a = 0; a < NC; ++a) {
+#pragma unroll
+                    for (int b = 0; b < NC; ++b) {
+                        if (mu == nu && b < a) continue;
+                        const int pf = mu * NC + a, qf = nu * NC + b;
+                        const int pr = pf * nf - pf * (pf - 1) / 2 + (qf - pf);
+                        C sv = S[(size_t)pr * p.g.ncell_h + kidx];
+                        if (conj) sv = cconj(sv);
+                        const T w = (pf == qf) ? T(1) : T(2);
+                        const C D = cscale(cmul(ekk, sv), w);
+                        const int c = NC == 3 ? (a <= b ? (a == 0 ? b : (a == 1 ? 2 + b : 5)) : (b == 0 ? a : (b == 1 ? 2 + a : 5))) : 0;
+#pragma unroll
+                        for (int r = 0; r < D3; ++r) acc[r][c] += E[r].x * D.x - E[r].y * D.y;
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < D3; ++r) {
+            const int rho3 = r0 + r;
+            if (rho3 >= d3) break;
+            int t3 = rho3 - lo3_mod;
+            if (t3 < 0) t3 += d3;
+            const int h3s = lo3 + t3;
+            if (h3s > h3hi) continue;
+            const int nv3 = (h3hi - h3s) / d3 + 1;
+            const int G3s = G3b + n3 * h3s;
+            // class sums over component pairs (00, 01 + 10, 02 + 20, 11, 12 + 21, 22) times the norm
+            T cm[NSYM];
+#pragma unroll
+            for (int c = 0; c < NSYM; ++c) cm[c] = acc[r][c] * norm;
+            const T tr = NC == 3 ? cm[0] + cm[3] + cm[5] : cm[0];
+            for (int h1 = rho1; h1 < gm.nH[0]; h1 += d1) {
+                const int G1 = G1b + n1 * h1;
+                if (G1 < g01 || G1 >= g01 + cnt1) continue;
+                for (int h2 = rho2; h2 < gm.nH[1]; h2 += d2) {
+                    const int G2 = G2b + n2 * h2;
+                    if (G2 < g02 || G2 >= g02 + cnt2) continue;
+                    T *row = p.out + ((size_t)(G1 - g01) * cnt2 + (G2 - g02)) * cnt3 + (G3s - g03);
+                    T Qs[3];
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) Qs[a] = fma((T)G3s, qs[6 + a], fma((T)G1, qs[a], (T)G2 * qs[3 + a]));
+                    for (int i3 = 0; i3 < nv3; ++i3) {
+                        T Qv[3];
+#pragma unroll
+                        for (int a = 0; a < 3; ++a) Qv[a] = fma((T)(i3 * stride), qs[6 + a], Qs[a]);
+                        const T q2 = Qv[0] * Qv[0] + Qv[1] * Qv[1] + Qv[2] * Qv[2];
+                        T val = tr;
+                        if (NC == 3) {
+                            // the off-diagonal sums already hold both orders (a, b) and (b, a)
+                            const T qcq = cm[0] * Qv[0] * Qv[0] + cm[3] * Qv[1] * Qv[1] + cm[5] * Qv[2] * Qv[2] +
+                                          cm[1] * Qv[0] * Qv[1] + cm[2] * Qv[0] * Qv[2] + cm[4] * Qv[1] * Qv[2];
+                            val = q2 > T(0) ? tr - div_w(qcq, q2) : T(2) / T(3) * tr;
+                        }
+                        if (p.ff.cls_kind[0] != 0) {
+                            const T f = form_factor<T>(p.ff.cls_kind[0], p.ff.cls_coef[0], q2 * (T)(1.0 / (FOUR_PI_D * FOUR_PI_D)));
+                            val *= f * f;
+                        }
+                        row[(size_t)i3 * stride] = val;
+                    }
+                }
+            }
+        }
+    }
+}
+
 }  // namespace
 
 template <typename T>
@@ -257,7 +394,28 @@ ds_status subbox_run(ds_model *M, const ds_qgrid *q, const ds_opts *o, T *d_out,
     if (kind == SRC_SPIN) norm *= 0.07265;  // C of Eq. mag_intensity (barn)
     p.norm = (T)norm;
     p.out = d_out;
-    {
+    const bool res = p.ff.ncls == 1 && residue_classes(M, gm, p.dres) &&
+                     (size_t)p.dres[2] * nsite * sizeof(C) + (size_t)nsite * 128 * sizeof(C) <= 96 * 1024 &&
+                     (long long)p.dres[0] * p.dres[1] * p.dres[2] <= 65535;
+    if (res) {
+        ProfScope ps(ctx, "subbox_recombine", st);
+        constexpr int D3 = 4;
+        const int ktiles = (g.ncell + 127) / 128;
+        const int d12 = p.dres[0] * p.dres[1], nchunk = (p.dres[2] + D3 - 1) / D3;
+        int s3 = nchunk;
+        for (int c = 1; c <= nchunk; ++c)
+            if (nchunk % c == 0 && (long long)ktiles * d12 * c >= 152LL * 4) { s3 = c; break; }
+        const size_t sm = ((size_t)p.dres[2] * nsite + (size_t)nsite * 128) * sizeof(C);
+        dim3 grid((unsigned)ktiles, (unsigned)(d12 * s3));
+        if (NC == 1) {
+            if (sm > 48 * 1024) cudaFuncSetAttribute(k_subbox_res<T, 1, D3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+            k_subbox_res<T, 1, D3><<<grid, 128, sm, st>>>(p, S, s3);
+        } else {
+            if (sm > 48 * 1024) cudaFuncSetAttribute(k_subbox_res<T, 3, D3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+            k_subbox_res<T, 3, D3><<<grid, 128, sm, st>>>(p, S, s3);
+        }
+        count_launches(1);
+    } else {
         ProfScope ps(ctx, "subbox_recombine", st);
         const long long nv = (long long)cnt[0] * cnt[1] * cnt[2];
         const unsigned nb = (unsigned)((nv + 255) / 256);

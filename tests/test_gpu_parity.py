@@ -414,6 +414,21 @@ def test_subbox_against_brute_force(ctx, disorder, kind, nsb, mode):
         assert rel_err_of_peak(got, want) < TOL[tag]
 
 
+@pytest.mark.parametrize("disorder,kind,ff,mode", [("occ", 0, "const", 1), ("spin", 1, "one_j0", 0),
+                                                   ("spin", 1, "const", 1)])
+def test_subbox_residue_classes_against_brute_force(ctx, disorder, kind, ff, mode):
+    """Sub-boxes on special positions (periods 4, 3, 2; one form-factor class): the library forms
+    the pair contraction once per residue class of zones; against the oracle's literal loop over
+    origins, FP64 and FP32."""
+    m = _special_positions_case(kind, 6, ff, 300 + kind)
+    q = m.qgrid
+    lm = to_library(ctx, m)
+    want = noise.subbox_intensity(m, disorder, mode, 2, q.g_index(m.cells) / np.array(m.cells, dtype=float))
+    for prec, tag in PREC:
+        got, _ = lm.intensity(qgrid_tuple(q), disorder=kind, mode=mode, precision=prec, smoothing=2, subbox_n=2)
+        assert rel_err_of_peak(got, want) < TOL[tag]
+
+
 # ----------------------------------------------------------------------------------------------
 # adjoint
 # ----------------------------------------------------------------------------------------------
