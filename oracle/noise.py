@@ -117,3 +117,59 @@ def lanczos_resample(intensity_at_G, Q: np.ndarray, m: int, mprime: int = 2) -> 
     uniq, inv = np.unique(G.reshape(-1, 3), axis=0, return_inverse=True)
     IG = np.asarray(intensity_at_G(uniq), dtype=np.float64)[inv.reshape(-1)].reshape(W.shape)
     return np.sum(W * IG, axis=1) / np.sum(W, axis=1)
+
+
+# ----------------------------------------------------------------------------------------------
+# spherically symmetric cutoff (Section V B, the last of the three modifications)
+# ----------------------------------------------------------------------------------------------
+
+
+def inscribed_radius(model) -> float:
+    """|r_max|: radius of the largest sphere inscribed in the supercell, half the smallest
+    distance between opposite faces; the faces normal to a*_alpha are n_alpha 2 pi / |a*_alpha|
+    apart."""
+    B = core.reciprocal_vectors(model.lattice)
+    return min(math.pi * n / float(np.linalg.norm(B[a])) for a, n in enumerate(model.cells))
+
+
+def sphere_cutoff_radius(model, m: int, mprime: int = 2) -> float:
+    """|r_c| = (1 - 1/m) |r_max|, scaled by 2/m' for the variant that decays to zero earlier
+    (m' = 2 is the paper's expression)."""
+    return (1.0 - 1.0 / m) * inscribed_radius(model) * 2.0 / mprime
+
+
+def sphere_weight(qdist: np.ndarray, rc: float) -> np.ndarray:
+    """W_r(|Q - G|) up to its constant prefactor: sin x / x^3 - cos x / x^2, x = |Q - G| |r_c|,
+    with its limit 1/3 at x = 0 (series below x = 1e-3)."""
+    x = np.asarray(qdist, dtype=np.float64) * rc
+    small = np.abs(x) < 1e-3
+    xs = np.where(small, 1.0, x)
+    exact = np.sin(xs) / xs ** 3 - np.cos(xs) / xs ** 2
+    return np.where(small, 1.0 / 3.0 - x * x / 30.0, exact)
+
+
+def sphere_lanczos_weight(model, dQ: np.ndarray, m: int, mprime: int = 2) -> np.ndarray:
+    """W = W_r(|Q - G|) L(Q - G): the spherical cutoff in place of Eq. weight_sinc, with the window
+    L of Eq. lanczos (m replaced by m m'/2); dQ = Q - G in supercell-index units [..., 3]."""
+    _, meff = lanczos_parameters(m, mprime)
+    dQ = np.asarray(dQ, dtype=np.float64)
+    n = np.asarray(model.cells, dtype=np.float64)
+    dcart = (dQ / n) @ core.reciprocal_vectors(model.lattice)
+    wr = sphere_weight(np.linalg.norm(dcart, axis=-1), sphere_cutoff_radius(model, m, mprime))
+    inside = np.all(np.abs(dQ) < meff, axis=-1)
+    L = np.where(inside, np.prod(sinc(math.pi * dQ / meff), axis=-1), 0.0)
+    return wr * L
+
+
+def sphere_resample(model, intensity_at_G, Q: np.ndarray, m: int, mprime: int = 2) -> np.ndarray:
+    """Eq. intensity_convol_finite with W = W_r L over the same (2m)^3 Bragg positions as the
+    separable window; Q in supercell-index units [nq, 3]."""
+    Q = np.asarray(Q, dtype=np.float64)
+    off = lanczos_support(Q, m, mprime)
+    base = np.floor(Q).astype(np.int64)
+    G = base[:, None, :] + off[None, :, :]
+    W = sphere_lanczos_weight(model, Q[:, None, :] - G, m, mprime)
+    uniq, inv = np.unique(G.reshape(-1, 3), axis=0, return_inverse=True)
+    IG = np.asarray(intensity_at_G(uniq), dtype=np.float64)[inv.reshape(-1)].reshape(W.shape)
+    return np.sum(W * IG, axis=1) / np.sum(W, axis=1)
+

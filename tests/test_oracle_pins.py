@@ -384,6 +384,37 @@ def test_lanczos_weights_and_normalisation():
     np.testing.assert_allclose(w8 / w8[7], fej, rtol=1e-12, atol=1e-15)
 
 
+def test_sphere_cutoff_is_the_fourier_transform_of_a_ball():
+    """Section V B, spherical cutoff: sin x/x^3 - cos x/x^2 (x = q r_c) is the Fourier transform of
+    the ball |r| < r_c divided by 4 pi r_c^3 -- checked against a radial quadrature of
+    int_0^rc 4 pi r^2 sin(q r)/(q r) dr, and its x -> 0 limit 1/3 (the ball volume)."""
+    from scipy.integrate import quad
+    rc = 7.3
+    for q in (1e-6, 0.05, 0.4, 1.3, 2.9):
+        ball = quad(lambda r: 4 * math.pi * r * r * (math.sin(q * r) / (q * r)), 0.0, rc, limit=200)[0]
+        assert math.isclose(float(noise.sphere_weight(np.array([q]), rc)[0]) * 4 * math.pi * rc ** 3, ball,
+                            rel_tol=1e-9, abs_tol=1e-9 * rc ** 3)
+    assert math.isclose(float(noise.sphere_weight(np.array([0.0]), rc)[0]), 1.0 / 3.0)
+
+
+def test_sphere_resample_constant_and_isotropy():
+    """The spherical window reproduces a constant intensity, depends only on |Q - G| (cubic cell:
+    permuting the axes of I(G) and of Q permutes nothing in the result), and the inscribed radius
+    of a cubic supercell is half its edge."""
+    m = syn.small_case(syn.OCC, cells=(4, 4, 4), nsite=1, nmodels=1, seed=3)
+    m.lattice = (5.0, 5.0, 5.0, 90.0, 90.0, 90.0)
+    assert math.isclose(noise.inscribed_radius(m), 10.0, rel_tol=1e-12)
+    rng = np.random.default_rng(4)
+    Q = rng.uniform(-6, 6, (40, 3))
+    out = noise.sphere_resample(m, lambda G: np.full(G.shape[0], 2.5), Q, 2)
+    assert np.allclose(out, 2.5, rtol=1e-12)
+    f = lambda G: np.cos(0.3 * G[:, 0]) + 0.1 * G[:, 1] ** 2 + np.sin(G[:, 2])
+    fp = lambda G: f(G[:, [1, 2, 0]])
+    a = noise.sphere_resample(m, f, Q, 2)
+    b = noise.sphere_resample(m, fp, Q[:, [2, 0, 1]], 2)
+    assert np.allclose(a, b, rtol=1e-12)
+
+
 def test_lanczos_resample_separable():
     """Separable application along each axis in turn (Section V B) equals the 3D sum."""
     rng = np.random.default_rng(7)
