@@ -65,8 +65,11 @@ enum { DS_TOTAL = 0, DS_DIFFUSE = 1 };
 /* DS_FP64: all arithmetic in double (the plain reference path).  DS_FP32: FFTs, tables and
  * recombination in float, tables generated in double. */
 enum { DS_FP64 = 0, DS_FP32 = 1 };
-/* noise reduction (Section V) */
-enum { DS_SMOOTH_NONE = 0, DS_SMOOTH_LANCZOS = 1, DS_SMOOTH_SUBBOX = 2 };
+/* noise reduction (Section V).  DS_SMOOTH_SPHERE: the Lanczos resampling with the spherically
+ * symmetric cutoff W_r(|Q - G|) in place of Eq. weight_sinc (the last modification of Section
+ * V B): W = W_r L, |r_c| = (1 - 1/m) |r_max| (times 2/m' for m' > 2), |r_max| the radius of the
+ * sphere inscribed in the supercell; not separable, so m m' <= 16 on the grid of Bragg positions. */
+enum { DS_SMOOTH_NONE = 0, DS_SMOOTH_LANCZOS = 1, DS_SMOOTH_SUBBOX = 2, DS_SMOOTH_SPHERE = 3 };
 
 /* grid of wavevectors in r.l.u.  Only commensurate grids are handled: step = 1/n_alpha and
  * h0 * n_alpha integral (the supercell Bragg positions of Eq. G_def, Section II). */
@@ -83,7 +86,7 @@ typedef struct {
     int taylor_order;   /* displacive: order P; < 0 chooses the smallest P whose remainder
                            bound x_max^(P+1)/(P+1)! <= taylor_eps (Section III C) */
     double taylor_eps;
-    int smoothing;      /* DS_SMOOTH_NONE, DS_SMOOTH_LANCZOS, DS_SMOOTH_SUBBOX */
+    int smoothing;      /* DS_SMOOTH_NONE, DS_SMOOTH_LANCZOS, DS_SMOOTH_SUBBOX, DS_SMOOTH_SPHERE */
     int lanczos_m;      /* m >= 2 of Eq. lanczos */
     int lanczos_mprime; /* m' >= 2 (2 = the plain window; r_cut = (1 - 1/m)/m') */
     int subbox_n;       /* n_sb of Section V A, 1 <= n_sb <= n_alpha/2 */
@@ -153,7 +156,7 @@ ds_status ds_request_intensity(ds_model *model, const ds_qgrid *grid, const ds_o
  * or (hkl_is_device) the device; out: npts values of the precision's type, host or device.  Each
  * point is resampled from I(G) on the supercell Bragg positions around it by Eq.
  * intensity_convol_finite with W = W_sinc L (Eqs. weight_sinc, windowed_sinc, lanczos;
- * opts->smoothing must be DS_SMOOTH_LANCZOS, with lanczos_m and lanczos_mprime): the sum runs
+ * opts->smoothing must be DS_SMOOTH_LANCZOS or DS_SMOOTH_SPHERE, with lanczos_m and lanczos_mprime): the sum runs
  * over floor(Q_a) - M + 1 <= G_a <= floor(Q_a) + M, M = ceil(m m'/2), inside the strict window
  * |Q_a - G_a| < m m'/2 (Q_a = n_a h_a).  I(G) is computed by the FFT method on the box of Bragg
  * positions that covers every point's support.  The call returns when the values are written

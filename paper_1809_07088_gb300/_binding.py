@@ -17,7 +17,7 @@ DS_FF_CONST, DS_FF_GAUSS4, DS_FF_J0 = 0, 1, 2
 DS_OCC, DS_SPIN, DS_DISP = 0, 1, 2
 DS_TOTAL, DS_DIFFUSE = 0, 1
 DS_FP64, DS_FP32 = 0, 1
-DS_SMOOTH_NONE, DS_SMOOTH_LANCZOS, DS_SMOOTH_SUBBOX = 0, 1, 2
+DS_SMOOTH_NONE, DS_SMOOTH_LANCZOS, DS_SMOOTH_SUBBOX, DS_SMOOTH_SPHERE = 0, 1, 2, 3
 
 _STATUS = {0: "DS_OK", -1: "DS_ERR_ARG", -2: "DS_ERR_STATE", -3: "DS_ERR_OOM", -4: "DS_ERR_ADMISSION",
            -5: "DS_ERR_TIMEOUT", -6: "DS_ERR_CUDA", -7: "DS_ERR_UNSUPPORTED"}

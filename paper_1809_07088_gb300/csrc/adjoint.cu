@@ -122,7 +122,17 @@ __device__ __forceinline__ c_t<T> site_amp(const RecombParams<T> &p, int s, cons
 
 constexpr int ADJ_ZC = 32;  // zones staged per chunk
 
-// Z_{m,mu,t}(k) for the displacive path; sorted site positions, full k index
+// acc += c b for a real c and a complex b: one paired FMA (FFMA2) in FP32
+__device__ __forceinline__ void acc_cb(float2 &acc, float c, float2 b) {
+    acc = __ffma2_rn(make_float2(c, c), b, acc);
+}
+__device__ __forceinline__ void acc_cb(double2 &acc, double c, double2 b) {
+    acc.x = fma(c, b.x, acc.x);
+    acc.y = fma(c, b.y, acc.y);
+}
+
+// Z_{m,mu,t}(k) for the displacive path; sorted site positions, full k index.  MAXS: sites held
+// per thread (exact site count up to 8)
 template <typename T, int MAXS, int TPT>
 __global__ void __launch_bounds__(256) k_adj_z_disp(const __grid_constant__ RecombParams<T> p, const T *dLdI,
                                                    const c_t<T> *F, int P, double scale, c_t<T> *Z) {
@@ -171,11 +181,11 @@ __global__ void __launch_bounds__(256) k_adj_z_disp(const __grid_constant__ Reco
                 Qd[a] = (double)G[0] / g.n[0] * p.recip[a] + (double)G[1] / g.n[1] * p.recip[3 + a] +
                         (double)G[2] / g.n[2] * p.recip[6 + a];
             if (part < 3) {
-                const double qs = Qd[part] / p.qscale;
+                const T qs = (T)(Qd[part] / p.qscale);  // |qs| <= 1
                 T *dst = pw + ((size_t)zi * 3 + part) * (P + 1);
-                double v = 1.0;
+                T v = T(1);
                 for (int q = 0; q <= P; ++q) {
-                    dst[q] = (T)v;
+                    dst[q] = v;
                     v *= qs;
                 }
             } else {
@@ -201,10 +211,7 @@ __global__ void __launch_bounds__(256) k_adj_z_disp(const __grid_constant__ Reco
                 if (s < p.nsite) {
                     const C b = beta[(size_t)zi * p.nsite + s];
 #pragma unroll
-                    for (int j = 0; j < TPT; ++j) {
-                        acc[j][s].x = fma(c[j], b.x, acc[j][s].x);
-                        acc[j][s].y = fma(c[j], b.y, acc[j][s].y);
-                    }
+                    for (int j = 0; j < TPT; ++j) acc_cb(acc[j][s], c[j], b);
                 }
             }
         }
@@ -366,17 +373,21 @@ ds_status backward_run(ds_model *M, const ds_qgrid *q, const ds_opts *o, const T
             } else {
                 constexpr int TPT = sizeof(T) == 4 ? 4 : 2;
                 const size_t sm = (size_t)ADJ_ZC * nsite * sizeof(C) + (size_t)ADJ_ZC * 3 * (keep.src.P + 1) * sizeof(T);
-                dim3 grid(g.ncell, (nT + 256 * TPT - 1) / (256 * TPT));
-                if (nsite <= 4) {
-                    if (sm > 48 * 1024) cudaFuncSetAttribute(k_adj_z_disp<T, 4, TPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-                    k_adj_z_disp<T, 4, TPT><<<grid, 256, sm, st>>>(p, dLdI, F, keep.src.P, 2.0 / (nmod * N), Z);
-                } else if (nsite <= 8) {
-                    if (sm > 48 * 1024) cudaFuncSetAttribute(k_adj_z_disp<T, 8, TPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-                    k_adj_z_disp<T, 8, TPT><<<grid, 256, sm, st>>>(p, dLdI, F, keep.src.P, 2.0 / (nmod * N), Z);
-                } else {
-                    if (sm > 48 * 1024) cudaFuncSetAttribute(k_adj_z_disp<T, 16, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-                    dim3 grid1(g.ncell, (nT + 255) / 256);
-                    k_adj_z_disp<T, 16, 1><<<grid1, 256, sm, st>>>(p, dLdI, F, keep.src.P, 2.0 / (nmod * N), Z);
+                auto launch = [&](auto kern, int tpt) {
+                    if (sm > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+                    dim3 gr(g.ncell, (nT + 256 * tpt - 1) / (256 * tpt));
+                    kern<<<gr, 256, sm, st>>>(p, dLdI, F, keep.src.P, 2.0 / (nmod * N), Z);
+                };
+                switch (nsite) {
+                    case 1: launch(k_adj_z_disp<T, 1, TPT>, TPT); break;
+                    case 2: launch(k_adj_z_disp<T, 2, TPT>, TPT); break;
+                    case 3: launch(k_adj_z_disp<T, 3, TPT>, TPT); break;
+                    case 4: launch(k_adj_z_disp<T, 4, TPT>, TPT); break;
+                    case 5: launch(k_adj_z_disp<T, 5, TPT>, TPT); break;
+                    case 6: launch(k_adj_z_disp<T, 6, TPT>, TPT); break;
+                    case 7: launch(k_adj_z_disp<T, 7, TPT>, TPT); break;
+                    case 8: launch(k_adj_z_disp<T, 8, TPT>, TPT); break;
+                    default: launch(k_adj_z_disp<T, 16, 1>, 1); break;
                 }
             }
             count_launches(1);

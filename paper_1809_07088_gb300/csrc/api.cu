@@ -618,9 +618,11 @@ ds_status check_request(ds_model *M, const ds_qgrid *q, const ds_opts *o) {
     if (o->disorder == DS_SPIN && !M->has_spins) return ds_fail(ctx, DS_ERR_STATE, "no spins uploaded");
     if (o->disorder == DS_DISP && !M->has_disp) return ds_fail(ctx, DS_ERR_STATE, "no displacements uploaded");
     if (o->disorder < 0 || o->disorder > 2) return ds_fail(ctx, DS_ERR_ARG, "disorder");
-    if (o->smoothing == DS_SMOOTH_LANCZOS) {
+    if (o->smoothing == DS_SMOOTH_LANCZOS || o->smoothing == DS_SMOOTH_SPHERE) {
         if (o->lanczos_m < 2 || o->lanczos_mprime < 2 || o->lanczos_m * o->lanczos_mprime > 64)
             return ds_fail(ctx, DS_ERR_ARG, "lanczos m, m' must be >= 2 with m m' <= 64");
+        if (o->smoothing == DS_SMOOTH_SPHERE && o->lanczos_m * o->lanczos_mprime > 16)
+            return ds_fail(ctx, DS_ERR_UNSUPPORTED, "the spherical cutoff handles m m' <= 16");
     } else if (o->smoothing == DS_SMOOTH_SUBBOX) {
         if (o->disorder == DS_DISP)
             return ds_fail(ctx, DS_ERR_UNSUPPORTED, "sub-box averaging is implemented for occupancy and spin disorder");
@@ -657,6 +659,58 @@ void box_corners(const ds_model *M, const int g0[3], const int cnt[3], double co
             }
 }
 
+// Lanczos resampling with either cutoff (both need the halo of I(G) around the grid)
+bool lanczos_like(const ds_opts *o) {
+    return o->smoothing == DS_SMOOTH_LANCZOS || o->smoothing == DS_SMOOTH_SPHERE;
+}
+
+// |r_c| = (1 - 1/m) |r_max| (2/m' for the variant decaying earlier); |r_max| = the radius of the
+// sphere inscribed in the supercell = half the smallest distance n_a 2 pi / |a*_a| between faces
+double sphere_cutoff_radius(const ds_model *M, int m, int mprime) {
+    const double pi = 3.141592653589793238462643383279502884;
+    double rmax = 1e300;
+    for (int a = 0; a < 3; ++a) {
+        const double bn = sqrt(M->recip[3 * a] * M->recip[3 * a] + M->recip[3 * a + 1] * M->recip[3 * a + 1] +
+                               M->recip[3 * a + 2] * M->recip[3 * a + 2]);
+        rmax = std::min(rmax, pi * M->n[a] / bn);
+    }
+    return (1.0 - 1.0 / m) * rmax * 2.0 / mprime;
+}
+
+// sin x / x^3 - cos x / x^2 (x = |Q - G| |r_c|), the spherical cutoff without its prefactor
+double sphere_profile(double x) {
+    if (fabs(x) < 1e-3) return 1.0 / 3.0 - x * x / 30.0;
+    return sin(x) / (x * x * x) - cos(x) / (x * x);
+}
+
+// normalised (2h+1)^3 stencil of W = W_r(|d|) L(d) over integer offsets d of Bragg positions
+void sphere_stencil_weights(const ds_model *M, int m, int mprime, int h, std::vector<double> &w) {
+    const double pi = 3.141592653589793238462643383279502884;
+    const double meff = 0.5 * m * mprime, rc = sphere_cutoff_radius(M, m, mprime);
+    const int nt = 2 * h + 1;
+    w.assign((size_t)nt * nt * nt, 0.0);
+    auto win = [&](int d) {
+        if (!(fabs((double)d) < meff)) return 0.0;
+        if (d == 0) return 1.0;
+        const double x = pi * d / meff;
+        return sin(x) / x;
+    };
+    double sum = 0.0;
+    for (int i = 0; i < nt; ++i)
+        for (int j = 0; j < nt; ++j)
+            for (int l = 0; l < nt; ++l) {
+                const int d[3] = {i - h, j - h, l - h};
+                double q[3] = {0, 0, 0};
+                for (int a = 0; a < 3; ++a)
+                    for (int c = 0; c < 3; ++c) q[c] += (double)d[a] / M->n[a] * M->recip[3 * a + c];
+                const double qn = sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2]);
+                const double v = sphere_profile(qn * rc) * win(d[0]) * win(d[1]) * win(d[2]);
+                w[((size_t)i * nt + j) * nt + l] = v;
+                sum += v;
+            }
+    for (double &v : w) v /= sum;
+}
+
 // smallest order whose remainder bound x_max^(P+1)/(P+1)! <= eps over the computing grid
 // (the requested grid plus the Lanczos halo); reads x_max back from the device (synchronises st)
 ds_status resolve_taylor_order(ds_model *M, const ds_qgrid *q, const ds_opts *o, cudaStream_t st, Scratch &ws, int *P,
@@ -665,7 +719,7 @@ ds_status resolve_taylor_order(ds_model *M, const ds_qgrid *q, const ds_opts *o,
     int g0[3], cnt[3];
     ds_status rc = grid_indices(ctx, M, q, g0, cnt);
     if (rc != DS_OK) return rc;
-    const int halo = o->smoothing == DS_SMOOTH_LANCZOS ? lanczos_halo(o->lanczos_m, o->lanczos_mprime) : 0;
+    const int halo = lanczos_like(o) ? lanczos_halo(o->lanczos_m, o->lanczos_mprime) : 0;
     int eg0[3], ecnt[3];
     for (int a = 0; a < 3; ++a) {
         eg0[a] = g0[a] - halo;
@@ -713,7 +767,7 @@ size_t request_footprint(const ds_model *M, const ds_qgrid *q, const ds_opts *o,
     }
     const size_t fb = std::max<size_t>(1, std::min<size_t>(nf, (512ull << 20) / (ce * g.ncell_h)));
     bytes += (nf + fb) * g.ncell_h * ce;
-    if (o->smoothing == DS_SMOOTH_LANCZOS) {
+    if (lanczos_like(o)) {
         const int h = lanczos_halo(o->lanczos_m, o->lanczos_mprime);
         bytes += 3 * (cnt[0] + 2 * h) * (cnt[1] + 2 * h) * (cnt[2] + 2 * h) * es;
     }
@@ -786,7 +840,7 @@ ds_status plan_and_run(ds_model *M, const ds_qgrid *q, const ds_opts *o, T *d_ou
 
     // computing grid: extended by the Lanczos halo on every side
     int halo = 0;
-    if (o->smoothing == DS_SMOOTH_LANCZOS) halo = lanczos_halo(o->lanczos_m, o->lanczos_mprime);
+    if (lanczos_like(o)) halo = lanczos_halo(o->lanczos_m, o->lanczos_mprime);
     int eg0[3], ecnt[3];
     for (int a = 0; a < 3; ++a) {
         eg0[a] = g0[a] - halo;
@@ -1018,6 +1072,24 @@ ds_status enqueue_request(ds_model *M, const ds_qgrid *q, const ds_opts *o, T *d
             ProfScope ps(ctx, "lanczos", st);
             lanczos_resample<T>(ext, t1, t2, d_out, cnt, o->lanczos_m, o->lanczos_mprime, st);
         }
+    } else if (o->smoothing == DS_SMOOTH_SPHERE) {
+        const int h = lanczos_halo(o->lanczos_m, o->lanczos_mprime);
+        const size_t next = (size_t)(cnt[0] + 2 * h) * (cnt[1] + 2 * h) * (cnt[2] + 2 * h);
+        const int nt = 2 * h + 1;
+        T *ext = (T *)ws.get(sizeof(T) * next);
+        T *dw = (T *)ws.get(sizeof(T) * nt * nt * nt);
+        if (ws.failed) return ds_fail(ctx, DS_ERR_OOM, "device allocation failed (resampling buffers)");
+        std::vector<double> w;
+        sphere_stencil_weights(M, o->lanczos_m, o->lanczos_mprime, h, w);
+        std::vector<T> wt(w.begin(), w.end());
+        CK(cudaMemcpyAsync(dw, wt.data(), sizeof(T) * wt.size(), cudaMemcpyHostToDevice, st));
+        rc = plan_and_run<T>(M, q, o, ext, st, ws, info, nullptr, hint);
+        if (rc == DS_OK) {
+            ProfScope ps(ctx, "lanczos_sphere", st);
+            sphere_resample<T>(ext, dw, d_out, cnt, h, st);
+        }
+        // the host weights must outlive their asynchronous copy
+        CK(cudaStreamSynchronize(st));
     } else {
         rc = plan_and_run<T>(M, q, o, d_out, st, ws, info, nullptr, hint);
     }

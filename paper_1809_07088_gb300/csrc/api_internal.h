@@ -155,6 +155,11 @@ ds_status resolve_taylor_order(ds_model *M, const ds_qgrid *q, const ds_opts *o,
                                double *xmax, double *umax = nullptr);
 size_t request_footprint(const ds_model *M, const ds_qgrid *q, const ds_opts *o, int P);
 bool residue_classes(const ds_model *M, const ds::GridMap &gm, int dres[3]);
+// Lanczos resampling with the separable or the spherical cutoff (api.cu)
+bool lanczos_like(const ds_opts *o);
+double sphere_cutoff_radius(const ds_model *M, int m, int mprime);
+double sphere_profile(double x);
+void sphere_stencil_weights(const ds_model *M, int m, int mprime, int h, std::vector<double> &w);
 // sub-box averaging (subbox.cu)
 template <typename T>
 ds_status subbox_run(ds_model *M, const ds_qgrid *q, const ds_opts *o, T *d_out, cudaStream_t st, Scratch &ws,

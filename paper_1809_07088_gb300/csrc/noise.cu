@@ -204,6 +204,45 @@ void lanczos_resample(const T *ext, T *tmp1, T *tmp2, T *out, const int cnt[3], 
     launch(tmp2, out, 0);
 }
 
+// Spherical cutoff (not separable): one thread per output voxel, (2h+1)^3 taps with the
+// normalised weights staged in shared memory; consecutive threads take consecutive voxels of a
+// row, so every tap is a coalesced read of the halo-extended volume.
+template <typename T>
+__global__ void k_sphere_stencil(const T *__restrict__ ext, const T *__restrict__ wg, T *__restrict__ out, int c0,
+                                 int c1, int c2, int h) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *w = (T *)smem_raw;
+    const int nt = 2 * h + 1, nt3 = nt * nt * nt;
+    for (int i = threadIdx.x; i < nt3; i += blockDim.x) w[i] = wg[i];
+    __syncthreads();
+    const int e1 = c1 + 2 * h, e2 = c2 + 2 * h;
+    const size_t total = (size_t)c0 * c1 * c2;
+    for (size_t v = (size_t)blockIdx.x * blockDim.x + threadIdx.x; v < total; v += (size_t)gridDim.x * blockDim.x) {
+        const int i2 = (int)(v % c2), i1 = (int)((v / c2) % c1), i0 = (int)(v / ((size_t)c2 * c1));
+        T acc = T(0);
+        for (int t0 = 0; t0 < nt; ++t0)
+            for (int t1 = 0; t1 < nt; ++t1) {
+                const T *row = ext + ((size_t)(i0 + t0) * e1 + (i1 + t1)) * e2 + i2;
+                const T *wr = w + (t0 * nt + t1) * nt;
+                for (int t2 = 0; t2 < nt; ++t2) acc = fma(wr[t2], row[t2], acc);
+            }
+        out[v] = acc;
+    }
+}
+
+template <typename T>
+void sphere_resample(const T *ext, const T *w, T *out, const int cnt[3], int h, cudaStream_t s) {
+    const size_t tot = (size_t)cnt[0] * cnt[1] * cnt[2];
+    const int nt = 2 * h + 1;
+    const size_t sm = (size_t)nt * nt * nt * sizeof(T);
+    if (sm > 48 * 1024) cudaFuncSetAttribute(k_sphere_stencil<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    const unsigned nb = (unsigned)std::max<size_t>(1, std::min<size_t>((tot + 255) / 256, 152 * 16));
+    k_sphere_stencil<T><<<nb, 256, sm, s>>>(ext, w, out, cnt[0], cnt[1], cnt[2], h);
+    count_launches(1);
+}
+
+template void sphere_resample<float>(const float *, const float *, float *, const int *, int, cudaStream_t);
+template void sphere_resample<double>(const double *, const double *, double *, const int *, int, cudaStream_t);
 template void lanczos_resample<float>(const float *, float *, float *, float *, const int *, int, int, cudaStream_t);
 template void lanczos_resample<double>(const double *, double *, double *, double *, const int *, int, int,
                                        cudaStream_t);

@@ -13,4 +13,8 @@ int lanczos_halo(int m, int mprime);
 template <typename T>
 void lanczos_resample(const T *ext, T *tmp1, T *tmp2, T *out, const int cnt[3], int m, int mprime, cudaStream_t s);
 
+// ext as above, w: normalised (2h+1)^3 stencil on the device; out: [cnt0][cnt1][cnt2]
+template <typename T>
+void sphere_resample(const T *ext, const T *w, T *out, const int cnt[3], int h, cudaStream_t s);
+
 }  // namespace ds

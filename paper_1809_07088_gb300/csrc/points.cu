@@ -8,7 +8,7 @@
 //     I(Q) = sum_G W(Q - G) I(G) / sum_G W(Q - G)
 // over floor(Q_a) - M + 1 <= G_a <= floor(Q_a) + M, M = ceil(m_eff), with the strict window
 // |Q_a - G_a| < m_eff.  W is a product of one-axis weights, so are its sums; the weights are
-// evaluated in FP64.
+// evaluated in FP64.  With the spherical cutoff W = W_r(|Q - G|) L(Q - G) is formed per tap.
 #include <algorithm>
 #include <climits>
 #include <cmath>
@@ -80,6 +80,52 @@ __global__ void k_lanczos_points(const T *__restrict__ vol, int b0, int b1, int 
     }
 }
 
+// spherical cutoff: W = W_r(|Q - G|) L(Q - G) per tap (not separable), FP64 weights
+struct SphereGeom {
+    double qstep[9];  // a*/n1, b*/n2, c*/n3 rows: Cartesian Q - G = sum_a (Q_a - G_a) qstep_a
+    double rc;        // |r_c|
+};
+
+template <typename T>
+__global__ void k_sphere_points(const T *__restrict__ vol, int b0, int b1, int b2, int c1, int c2,
+                                const double *__restrict__ Q, long long npts, int M, double meff,
+                                const __grid_constant__ SphereGeom sg, T *__restrict__ out) {
+    const int ntap = 2 * M;
+    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < npts;
+         p += (long long)gridDim.x * blockDim.x) {
+        const double q[3] = {Q[3 * p], Q[3 * p + 1], Q[3 * p + 2]};
+        const double fq[3] = {floor(q[0]), floor(q[1]), floor(q[2])};
+        double acc = 0.0, wsum = 0.0;
+        for (int t0 = 0; t0 < ntap; ++t0) {
+            const double d0 = q[0] - (fq[0] - M + 1 + t0);
+            if (!(fabs(d0) < meff)) continue;
+            const double l0 = d0 == 0.0 ? 1.0 : sinpi(d0 / meff) / (PI_D * d0 / meff);
+            for (int t1 = 0; t1 < ntap; ++t1) {
+                const double d1 = q[1] - (fq[1] - M + 1 + t1);
+                if (!(fabs(d1) < meff)) continue;
+                const double l1 = d1 == 0.0 ? 1.0 : sinpi(d1 / meff) / (PI_D * d1 / meff);
+                const T *row = vol + ((size_t)((int)fq[0] - M + 1 + t0 - b0) * c1 + ((int)fq[1] - M + 1 + t1 - b1)) * c2 +
+                               ((int)fq[2] - M + 1 - b2);
+                for (int t2 = 0; t2 < ntap; ++t2) {
+                    const double d2 = q[2] - (fq[2] - M + 1 + t2);
+                    if (!(fabs(d2) < meff)) continue;
+                    const double l2 = d2 == 0.0 ? 1.0 : sinpi(d2 / meff) / (PI_D * d2 / meff);
+                    double c[3];
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) c[a] = d0 * sg.qstep[a] + d1 * sg.qstep[3 + a] + d2 * sg.qstep[6 + a];
+                    const double x = sqrt(c[0] * c[0] + c[1] * c[1] + c[2] * c[2]) * sg.rc;
+                    const double wr = fabs(x) < 1e-3 ? 1.0 / 3.0 - x * x / 30.0
+                                                     : sin(x) / (x * x * x) - cos(x) / (x * x);
+                    const double w = wr * l0 * l1 * l2;
+                    acc += w * (double)row[t2];
+                    wsum += w;
+                }
+            }
+        }
+        out[p] = (T)(acc / wsum);
+    }
+}
+
 template <typename T>
 void launch_points(const T *vol, const int box[3], const int cnt[3], const double *dQ, long long npts, int M,
                    double rcut, double meff, T *out, cudaStream_t s) {
@@ -141,7 +187,15 @@ ds_status run_points(ds_model *Mdl, const std::vector<double> &Qh, long long npt
     if (rc != DS_OK) return rc;
     if (cudaMemcpyAsync(dQ, Qh.data(), sizeof(double) * 3 * npts, cudaMemcpyHostToDevice, st) != cudaSuccess)
         return ds_fail(ctx, DS_ERR_CUDA, "copy of the points failed");
-    {
+    if (o->smoothing == DS_SMOOTH_SPHERE) {
+        ProfScope ps(ctx, "lanczos_points", st);
+        SphereGeom sg;
+        for (int i = 0; i < 9; ++i) sg.qstep[i] = Mdl->recip[i] / Mdl->n[i / 3];
+        sg.rc = sphere_cutoff_radius(Mdl, m, mp);
+        const unsigned nb = (unsigned)std::max<long long>(1, std::min<long long>((npts + 127) / 128, 152 * 32));
+        k_sphere_points<T><<<nb, 128, 0, st>>>(vol, b[0], b[1], b[2], cnt[1], cnt[2], dQ, npts, M, meff, sg, dout);
+        count_launches(1);
+    } else {
         ProfScope ps(ctx, "lanczos_points", st);
         launch_points<T>(vol, b, cnt, dQ, npts, M, rcut, meff, dout, st);
     }
@@ -165,8 +219,8 @@ extern "C" ds_status ds_request_points(ds_model *Mdl, const double *hkl, int64_t
     if (!o) return ds_fail(ctx, DS_ERR_ARG, "null options");
     if (npts < 0) return ds_fail(ctx, DS_ERR_ARG, "negative point count");
     if (npts > 0 && (!hkl || !out)) return ds_fail(ctx, DS_ERR_ARG, "null points or output");
-    if (o->smoothing != DS_SMOOTH_LANCZOS)
-        return ds_fail(ctx, DS_ERR_ARG, "points off the Bragg grid need smoothing = DS_SMOOTH_LANCZOS");
+    if (o->smoothing != DS_SMOOTH_LANCZOS && o->smoothing != DS_SMOOTH_SPHERE)
+        return ds_fail(ctx, DS_ERR_ARG, "points off the Bragg grid need smoothing = DS_SMOOTH_LANCZOS or DS_SMOOTH_SPHERE");
     if (!Mdl->has_cells) return ds_fail(ctx, DS_ERR_STATE, "model incomplete");
     if (info) memset(info, 0, sizeof(*info));
     if (npts == 0) return DS_OK;

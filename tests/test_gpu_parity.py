@@ -233,6 +233,25 @@ def test_points_errors(ctx):
     assert out.shape == (0,) and info["nvox"] == 0
 
 
+@pytest.mark.parametrize("prec,tag", PREC)
+@pytest.mark.parametrize("m_,mp", [(2, 2), (3, 2), (2, 4), (3, 3)])
+def test_sphere_cutoff_commensurate_and_points(ctx, prec, tag, m_, mp):
+    """Spherically symmetric cutoff W_r(|Q - G|) with the Lanczos window (Section V B): on the grid
+    of Bragg positions (3D stencil) and at arbitrary points, triclinic cell, against the oracle's
+    literal finite sum."""
+    m = syn.small_case(syn.OCC, cells=(6, 5, 4), nsite=3, nmodels=2, seed=141)
+    lm = to_library(ctx, m)
+    I_at = lambda G: core.occupancy_intensity_fft(m, G, 1)
+    got, _ = lm.intensity(qgrid_tuple(m.qgrid), disorder=0, mode=1, precision=prec, smoothing=3, lanczos_m=m_,
+                          lanczos_mprime=mp)
+    want = noise.sphere_resample(m, I_at, _G(m).astype(float), m_, mp)
+    assert rel_err_of_peak(got, want) < TOL[tag]
+    hkl = np.random.default_rng(12).uniform(-1.2, 1.2, (150, 3))
+    gp, _ = lm.intensity_points(hkl, disorder=0, mode=1, precision=prec, smoothing=3, lanczos_m=m_,
+                                lanczos_mprime=mp)
+    assert rel_err_of_peak(gp, noise.sphere_resample(m, I_at, hkl * np.array(m.cells), m_, mp)) < TOL[tag]
+
+
 def test_device_output_on_torch_stream(ctx):
     import torch
     m = syn.small_case(syn.OCC, cells=(6, 5, 4), nsite=3, nmodels=1, seed=107)
