@@ -552,6 +552,55 @@ def run_rows(dev):
     return rows
 
 
+def run_profile_workload(name):
+    """A small case of one row, run twice, for ncu captures (a few hundred MB on the device):
+    taylor = fcc 32^3, 321^3 voxels, P = 12; lanczos = occupancy 32^3 cells, 513^3 voxels,
+    m = 2, m' = 8; subbox = the pyrochlore occupancy volume with n_sb = 5."""
+    import ctypes
+    import numpy as np
+    import torch
+    import paper_1809_07088_gb300 as ds
+    import synthetic as syn
+    ctx = ds.Context(0)
+    if name == "taylor":
+        m = syn.displacive_fcc(cells=(32, 32, 32), sigma=0.1, seed=5)
+        m.qgrid = syn.symmetric_qgrid(5.0, m.cells)
+        lm = ds.Model(ctx, m.lattice, m.sites, m.cells, 1, m.scat_len, m.ff_kind, m.ff_coef)
+        lm.upload_displacements(np.ascontiguousarray(m.disp))
+        opts = dict(disorder=ds.DS_DISP, mode=ds.DS_TOTAL, precision=ds.DS_FP32, taylor_order=12)
+    elif name == "lanczos":
+        n = 32
+        m = syn.Model(lattice=(4.0, 4.0, 4.0, 90.0, 90.0, 90.0), sites=np.array([[0.0, 0.0, 0.0]]),
+                      scat_len=np.ones(1), ff_kind=np.zeros(1, dtype=np.int32), ff_coef=np.zeros((1, 9)),
+                      cells=(n, n, n), nmodels=1)
+        m.occ = (np.random.default_rng(3).random((1, 1, n, n, n)) < 0.5).astype(np.uint8)
+        m.qgrid = syn.symmetric_qgrid(8.0, m.cells)
+        lm = ds.Model(ctx, m.lattice, m.sites, m.cells, 1, m.scat_len, m.ff_kind, m.ff_coef)
+        lm.upload_occupancy(np.ascontiguousarray(m.occ))
+        opts = dict(disorder=ds.DS_OCC, mode=ds.DS_DIFFUSE, precision=ds.DS_FP32, smoothing=ds.DS_SMOOTH_LANCZOS,
+                    lanczos_m=2, lanczos_mprime=8)
+    else:
+        m = syn.pyrochlore_occ_mag()
+        lm = ds.Model(ctx, m.lattice, m.sites, m.cells, 1, m.scat_len, m.ff_kind, m.ff_coef)
+        lm.upload_occupancy(np.ascontiguousarray(m.occ))
+        opts = dict(disorder=ds.DS_OCC, mode=ds.DS_DIFFUSE, precision=ds.DS_FP32, smoothing=ds.DS_SMOOTH_SUBBOX,
+                    subbox_n=5)
+    q = (m.qgrid.h0, m.qgrid.step, m.qgrid.count)
+    out = torch.empty(m.qgrid.count, dtype=torch.float32, device="cuda")
+    lm.intensity(q, out=out, **opts)
+    torch.cuda.synchronize()
+    buf = ctypes.create_string_buffer(1 << 16)
+    ctx.lib.ds_profile_report(ctx.h, buf, len(buf))
+    ctx.lib.ds_profile_enable(ctx.h, 1)
+    lm.intensity(q, out=out, **opts)
+    torch.cuda.synchronize()
+    ctx.check(ctx.lib.ds_profile_report(ctx.h, buf, len(buf)))
+    print(json.dumps({"profile_workload": name, "stages": json.loads(buf.value.decode())["stages"]}))
+    lm.close()
+    ctx.close()
+    return 0
+
+
 # ----------------------------------------------------------------------------------------------
 # serving: Poisson arrivals of mixed requests through ds_submit / ds_wait
 # ----------------------------------------------------------------------------------------------
@@ -686,11 +735,15 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serving", type=int, default=128, help="requests in the serving stream (0 = skip)")
     ap.add_argument("--no-rows", action="store_true", help="skip the per-row measurements")
+    ap.add_argument("--profile-workload", choices=["taylor", "lanczos", "subbox"], default=None,
+                    help="run one small row workload twice (for ncu captures) and exit")
     ap.add_argument("--streams", type=int, default=2, choices=[1, 2],
                     help="2: the two volumes of a step on two streams (their kernels overlap)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    if args.profile_workload:
+        return run_profile_workload(args.profile_workload)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)
