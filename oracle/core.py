@@ -239,20 +239,52 @@ def perp_sq(F: np.ndarray, Q: np.ndarray) -> np.ndarray:
     return np.where(qn > 0, tot - par, (2.0 / 3.0) * tot)
 
 
-def magnetic_intensity_direct(model, hkl, mode=TOTAL) -> np.ndarray:
-    """I_mag = (C/N) < |F_perp|^2 >, F_mag = sum f_mag M_j exp(i G.r_j) (Eqs. mag_sf with T = 1,
-    mag_intensity, mag_projection).  DIFFUSE subtracts the structure factor of the mean moment
-    of each site (zero when the moments have no long-range order)."""
+def debye_waller(model, hkl, occupancy=False, chunk=2048) -> np.ndarray:
+    """T_mu(Q) of Eq. dw for every row of `hkl` and every site, [nq, nsite]: the mean over the
+    lattice points R and the supercells of (1 + a) exp(i Q.u_R,mu).  The odd orders of Q.u
+    average to zero over the ensemble (Section III C), so the even part, the mean of
+    (1 + a) cos(Q.u), is kept: the same reading as <F(H)> in `displacive_bragg`.  With
+    occupancy=True the weight 1 + a is the occupancy delta of each atom (when the model has
+    occupancies); otherwise it is 1 (the moments of the magnetic case carry their own size)."""
+    Q = q_cart(hkl, model.lattice)
+    out = np.zeros((Q.shape[0], model.nsite))
+    for mu in range(model.nsite):
+        u = model.disp[:, mu].reshape(-1, 3).astype(np.float64)          # [(model, R), 3]
+        w = np.ones(u.shape[0])
+        if occupancy and model.occ is not None:
+            w = model.occ[:, mu].reshape(-1).astype(np.float64)
+        for q0 in range(0, Q.shape[0], chunk):
+            out[q0:q0 + chunk, mu] = np.cos(Q[q0:q0 + chunk] @ u.T) @ w / u.shape[0]
+    return out
+
+
+def magnetic_intensity_direct(model, hkl, mode=TOTAL, dw=False) -> np.ndarray:
+    """I_mag = (C/N) < |F_perp|^2 >, F_mag = sum f_mag T_mu M_j exp(i G.r_j) (Eqs. mag_sf,
+    mag_intensity, mag_projection), T_mu = 1, or with dw=True the Debye-Waller factor of the
+    model's displacements (`debye_waller`), the only coupling of the moments to the
+    displacements in Eq. mag_sf.  DIFFUSE subtracts the structure factor of the mean moment of
+    each site (zero when the moments have no long-range order)."""
     frac, site = atom_list(model)
     Q = q_cart(hkl, model.lattice)
-    bragg = 0.0
-    if mode == DIFFUSE:
-        mbar = mean_moment(model) * model.ncell * model.scat_len[:, None]
-        bragg = _cell_sf(model, mbar, hkl) * is_integer_hkl(hkl)[:, None]
+    integer = is_integer_hkl(hkl)[:, None]
+    mbar = mean_moment(model) * model.ncell * model.scat_len[:, None]
+    T = debye_waller(model, hkl) if dw else None
     acc = np.zeros(hkl.shape[0])
     for m in range(model.nmodels):
         amp = model.spins[m].reshape(-1, 3).astype(np.float64) * model.scat_len[site][:, None]
-        F = _sf(model, frac, None, amp, site, hkl) - bragg
+        if T is None:
+            F = _sf(model, frac, None, amp, site, hkl)
+            if mode == DIFFUSE:
+                F = F - _cell_sf(model, mbar, hkl) * integer
+        else:
+            F = np.zeros((hkl.shape[0], 3), dtype=np.complex128)
+            for mu in range(model.nsite):
+                sel = site == mu
+                Fmu = _sf(model, frac[sel], None, amp[sel], site[sel], hkl)
+                if mode == DIFFUSE:
+                    Fmu = Fmu - _sf(model, model.sites[mu:mu + 1], None, mbar[mu:mu + 1],
+                                    np.array([mu]), hkl) * integer
+                F += T[:, mu, None] * Fmu
         acc += perp_sq(F, Q)
     return C_MAG * acc / (model.nmodels * model.natom)
 
@@ -307,15 +339,17 @@ def occupancy_intensity_fft(model, G, mode=DIFFUSE) -> np.ndarray:
     return np.mean(np.abs(F) ** 2, axis=0) / model.natom
 
 
-def magnetic_intensity_fft(model, G, mode=TOTAL) -> np.ndarray:
-    """Eqs. mag_sf (T = 1), mag_ft (one FFT per Cartesian component), mag_intensity,
-    mag_projection."""
+def magnetic_intensity_fft(model, G, mode=TOTAL, dw=False) -> np.ndarray:
+    """Eqs. mag_sf (T = 1, or with dw=True the Debye-Waller factor of Eq. dw from
+    `debye_waller`), mag_ft (one FFT per Cartesian component), mag_intensity, mag_projection."""
     M = model.spins.astype(np.float64)                    # [model][site][n1][n2][n3][3]
     if mode == DIFFUSE:
         M = M - mean_moment(model)[None, :, None, None, None, :]
     X = lattice_fft(np.moveaxis(M, -1, 2))                # [model][site][3][k1][k2][k3]
     k = split_G(G, model.cells)
     phi, Q = _phi(model, G)
+    if dw:
+        phi = phi * debye_waller(model, G / np.asarray(model.cells, dtype=np.float64))
     Xk = X[:, :, :, k[:, 0], k[:, 1], k[:, 2]]            # [model][site][3][nvox]
     acc = np.zeros(G.shape[0])
     for m in range(model.nmodels):

@@ -34,35 +34,71 @@ def subbox_fields(model, disorder: str, mode: int) -> np.ndarray:
     raise ValueError(disorder)
 
 
-def subbox_intensity(model, disorder: str, mode: int, nsb: int, hkl: np.ndarray) -> np.ndarray:
-    """Every lattice point o of the periodic supercell is the origin of one sub-box of nsb^3
-    cells with open boundaries (the every-lattice-point variant of Section V A); the box holds
-    the atoms of cells o + d, d in [0, nsb)^3, at their unwrapped positions o + d + r_mu, with the
-    amplitudes of the wrapped cells (o + d) mod n.  I(Q) = sum_o |F_o(Q)|^2 / (ncell nsite nsb^3),
-    averaged over supercells (magnetic: C |F_o,perp|^2, Eqs. mag_intensity, mag_projection)."""
-    x = subbox_fields(model, disorder, mode)
-    ncomp = x.shape[-1]
+def all_origins(model) -> np.ndarray:
+    """Every lattice point of every supercell, [(model, o1, o2, o3)] in C order."""
+    grids = np.meshgrid(np.arange(model.nmodels), *(np.arange(c) for c in model.cells),
+                        indexing="ij")
+    return np.stack([g.reshape(-1) for g in grids], -1)
+
+
+def subbox_intensity(model, disorder: str, mode: int, nsb: int, hkl: np.ndarray,
+                     origins=None) -> np.ndarray:
+    """Method of sub-boxes (Section V A).  Each origin (m, o) is the lattice point o of supercell
+    m; its sub-box holds the atoms of the nsb^3 cells o + d, d in [0, nsb)^3, with open
+    boundaries: at their unwrapped positions o + d + r_mu (+ u), with the data of the wrapped
+    cells (o + d) mod n.  I(Q) = sum_origins |F_o(Q)|^2 / (norigin nsite nsb^3), magnetic
+    C |F_o,perp|^2 (Eqs. mag_intensity, mag_projection).  origins=None: every lattice point of
+    every supercell (the every-lattice-point variant); else rows (m, o1, o2, o3), e.g. drawn at
+    random (the original random-origin variant).
+
+    disorder "occ" / "spin": amplitudes of `subbox_fields`.  "disp": the atom at o + d + r_mu
+    + u scatters with amplitude w = b delta (b without occupancies), exp(i Q.u) exact (no Taylor
+    expansion); DIFFUSE subtracts from each atom the site mean of w cos(Q.u), i.e. b T_mu(Q)
+    with `core.debye_waller(occupancy=True)`, so that nsb = n at a Bragg position of the
+    supercell gives F - <F> of `core.displacive_intensity_direct`."""
     n = np.asarray(model.cells)
     d = np.stack(np.meshgrid(*(np.arange(nsb),) * 3, indexing="ij"), -1).reshape(-1, 3)
     nbox_atoms = d.shape[0] * model.nsite
     site = np.repeat(np.arange(model.nsite), d.shape[0])
     Q = core.q_cart(hkl, model.lattice)
+    origins = all_origins(model) if origins is None else np.asarray(origins).reshape(-1, 4)
+    if disorder == "disp":
+        T = core.debye_waller(model, hkl, occupancy=True) if mode == core.DIFFUSE else None
+    else:
+        x = subbox_fields(model, disorder, mode)
+        ncomp = x.shape[-1]
     acc = np.zeros(hkl.shape[0])
-    origins = np.stack(np.meshgrid(*(np.arange(c) for c in model.cells), indexing="ij"),
-                       -1).reshape(-1, 3)
-    for m in range(model.nmodels):
-        for o in origins:
-            cells = o[None, :] + d                                   # unwrapped
-            wrapped = np.mod(cells, n)
-            frac = (cells[None, :, :] + model.sites[:, None, :]).reshape(-1, 3)
-            amp = x[m][:, wrapped[:, 0], wrapped[:, 1], wrapped[:, 2], :].reshape(nbox_atoms, ncomp)
-            F = core.structure_factor(frac, None, amp, site, model.ff_kind, model.ff_coef,
-                                      model.lattice, hkl)
-            if disorder == "spin":
-                acc += core.perp_sq(F, Q)
-            else:
-                acc += np.abs(F[:, 0]) ** 2
-    I = acc / (model.nmodels * model.ncell * model.nsite * nsb ** 3)
+    for row in origins:
+        m, o = int(row[0]), np.asarray(row[1:4])
+        cells = o[None, :] + d                                       # unwrapped
+        wrapped = np.mod(cells, n)
+        frac = (cells[None, :, :] + model.sites[:, None, :]).reshape(-1, 3)
+        if disorder == "disp":
+            u = model.disp[m][:, wrapped[:, 0], wrapped[:, 1], wrapped[:, 2], :]
+            u = u.reshape(nbox_atoms, 3).astype(np.float64)
+            w = np.repeat(model.scat_len.astype(np.float64), d.shape[0])
+            if model.occ is not None:
+                w = w * model.occ[m][:, wrapped[:, 0], wrapped[:, 1], wrapped[:, 2]].reshape(-1)
+            F = core.structure_factor(frac, u, w, site, model.ff_kind, model.ff_coef,
+                                      model.lattice, hkl)[:, 0]
+            if T is not None:
+                for mu in range(model.nsite):
+                    sel = site == mu
+                    Fmu = core.structure_factor(frac[sel], None,
+                                                np.full(d.shape[0], float(model.scat_len[mu])),
+                                                site[sel], model.ff_kind, model.ff_coef,
+                                                model.lattice, hkl)[:, 0]
+                    F = F - T[:, mu] * Fmu
+            acc += np.abs(F) ** 2
+            continue
+        amp = x[m][:, wrapped[:, 0], wrapped[:, 1], wrapped[:, 2], :].reshape(nbox_atoms, ncomp)
+        F = core.structure_factor(frac, None, amp, site, model.ff_kind, model.ff_coef,
+                                  model.lattice, hkl)
+        if disorder == "spin":
+            acc += core.perp_sq(F, Q)
+        else:
+            acc += np.abs(F[:, 0]) ** 2
+    I = acc / (origins.shape[0] * model.nsite * nsb ** 3)
     return core.C_MAG * I if disorder == "spin" else I
 
 

@@ -14,7 +14,9 @@ reciprocal-space points), since the paper's own Monte-Carlo supercells are not a
                          von Mises-Fisher unit spins around seeded local axes, <j0> form factor
 * ``perovskite_correlated`` cubic a = 4 A, 5 sites, Gaussian-filtered correlated displacements,
                          4-Gaussian X-ray-like form factors with seeded coefficients
+* ``pyrochlore_mag_disp`` the magnetic pyrochlore whose atoms also carry Gaussian displacements
 * ``serving_mix``        Poisson arrivals of mixed supercell sizes / disorder types
+* ``random_origins``, ``covering_origins``  seeded sub-box origins (model, o1, o2, o3)
 
 Array layouts (C order): occupancy uint8 [model][site][n1][n2][n3]; spins and displacements
 float32 [model][site][n1][n2][n3][3] (Cartesian; spins in Bohr magnetons, displacements in
@@ -220,6 +222,45 @@ def magnetic_view(m: Model) -> Model:
     return Model(lattice=m.lattice, sites=m.sites, scat_len=np.ones(m.nsite), ff_kind=kinds,
                  ff_coef=coef, cells=m.cells, nmodels=m.nmodels, spins=m.spins, qgrid=m.qgrid,
                  meta=dict(m.meta))
+
+
+def pyrochlore_mag_disp(cells=(20, 20, 20), kappa=2.0, sigma=0.05, seed=6, nmodels=1,
+                        hmax=6.0, nsite=16) -> Model:
+    """The magnetic pyrochlore (<j0> on every site, vMF spins) whose atoms also carry i.i.d.
+    Gaussian displacements (sigma per Cartesian component, Angstrom): the input of the
+    magnetic + displacive coupling through the Debye-Waller factor."""
+    m = magnetic_view(pyrochlore_occ_mag(cells=cells, kappa=kappa, seed=seed, nmodels=nmodels,
+                                         hmax=hmax, nsite=nsite))
+    m.disp = gaussian_displacements(_rng(seed + 500), nmodels, nsite, cells, sigma)
+    m.meta["kind"] = "mag+disp"
+    m.meta["sigma"] = sigma
+    return m
+
+
+def random_origins(rng, nmodels, cells, count) -> np.ndarray:
+    """`count` sub-box origins (model, o1, o2, o3), int32, uniform over the lattice points of
+    the ensemble."""
+    out = np.empty((count, 4), dtype=np.int32)
+    out[:, 0] = rng.integers(0, nmodels, count)
+    for a in range(3):
+        out[:, 1 + a] = rng.integers(0, cells[a], count)
+    return out
+
+
+def covering_origins(rng, nmodels, cells, nsb) -> np.ndarray:
+    """Random sub-box origins, drawn per supercell until each of its lattice points lies in at
+    least one box of nsb^3 cells (periodic wrap): the random-origin variant of the method of
+    sub-boxes (Section V A), whose count is set by that coverage rule."""
+    rows = []
+    span = np.arange(nsb)
+    for m in range(nmodels):
+        covered = np.zeros(cells, dtype=bool)
+        while not covered.all():
+            o = [int(rng.integers(0, c)) for c in cells]
+            idx = [np.mod(o[a] + span, cells[a]) for a in range(3)]
+            covered[np.ix_(*idx)] = True
+            rows.append((m, *o))
+    return np.asarray(rows, dtype=np.int32)
 
 
 def random_gauss4(rng, nsite) -> np.ndarray:

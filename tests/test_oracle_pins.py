@@ -497,6 +497,146 @@ def test_subbox_pair_sum_form():
     np.testing.assert_allclose(I, want, rtol=1e-10)
 
 
+def _box_sf_closed_form(m, hkl, nsb):
+    """sum_{d in [0, nsb)^3} exp(2 pi i hkl.d), a product of three geometric series."""
+    out = np.ones(hkl.shape[0], dtype=complex)
+    for a in range(3):
+        z = np.exp(2j * np.pi * hkl[:, a])
+        near = np.abs(z - 1.0) < 1e-12
+        safe = np.where(near, 0.5, z)
+        out *= np.where(near, nsb, (1.0 - safe ** nsb) / (1.0 - safe))
+    return out
+
+
+def test_subbox_displacive_without_displacements_is_occupational():
+    """u = 0: the displacive sub-box (amplitude b delta exp(i Q.u), DIFFUSE minus b <delta>)
+    reduces to the occupational one (b delta, DIFFUSE b (delta - c)) at any Q and origin set."""
+    m = syn.small_case(syn.DISP, cells=(4, 3, 5), nsite=3, nmodels=2, seed=61)
+    m.disp = np.zeros_like(m.disp)
+    rng = np.random.default_rng(3)
+    hkl = rng.uniform(-1.7, 1.7, (6, 3))
+    org = syn.random_origins(rng, m.nmodels, m.cells, 5)
+    for mode in (core.TOTAL, core.DIFFUSE):
+        for origins in (None, org):
+            a = noise.subbox_intensity(m, "disp", mode, 2, hkl, origins)
+            b = noise.subbox_intensity(m, "occ", mode, 2, hkl, origins)
+            np.testing.assert_allclose(a, b, rtol=1e-12, atol=1e-14)
+
+
+def test_subbox_displacive_rigid_shift_ensemble():
+    """Supercell 0 shifted rigidly by u0, supercell 1 by -u0 (no occupancies): |F_o| does not
+    change (TOTAL equals the undisplaced result), T_mu(Q) = cos(Q.u0) on every site, so each
+    atom scatters i b sin(Q.u0) exp(i Q.r) and DIFFUSE = sin^2(Q.u0) TOTAL(u = 0); the box sum
+    of one cell-uniform box is the closed-form geometric series."""
+    m = syn.small_case(syn.DISP, cells=(3, 4, 3), nsite=1, nmodels=2, seed=62)
+    m.ff_kind = np.zeros(1, dtype=np.int32)
+    u0 = np.array([0.11, -0.07, 0.05])
+    m.disp = np.zeros_like(m.disp)
+    m.disp[0] = u0
+    m.disp[1] = -u0
+    rng = np.random.default_rng(4)
+    hkl = rng.uniform(-2.0, 2.0, (8, 3))
+    nsb = 2
+    tot = noise.subbox_intensity(m, "disp", core.TOTAL, nsb, hkl)
+    dif = noise.subbox_intensity(m, "disp", core.DIFFUSE, nsb, hkl)
+    # one site, constant form factor: |F_o| = b |box series|, the same for every origin
+    want0 = m.scat_len[0] ** 2 * np.abs(_box_sf_closed_form(m, hkl, nsb)) ** 2 / nsb ** 3
+    np.testing.assert_allclose(tot, want0, rtol=1e-12)
+    qu = core.q_cart(hkl, m.lattice) @ m.disp[0, 0, 0, 0, 0].astype(np.float64)
+    np.testing.assert_allclose(dif, np.sin(qu) ** 2 * want0, rtol=1e-10, atol=1e-14)
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_subbox_whole_supercell_box_is_the_direct_sum(mode):
+    """n_sb = n: one box covers the whole supercell, so at a supercell Bragg position (where
+    exp(i G.R) is periodic) every origin gives F of the direct sum of its supercell (two origins
+    per supercell here, so that the supercells weigh equally), and DIFFUSE gives F - <F> with
+    <F> of Eq. bragg_sf_disp: I equals core.displacive_intensity_direct."""
+    m = syn.small_case(syn.DISP, cells=(3, 3, 3), nsite=2, nmodels=2, seed=63, sigma=0.12)
+    rng = np.random.default_rng(6)
+    G = rng.integers(-5, 6, (6, 3))
+    G[0] = (3, 0, -3)                      # an integer hkl: the Bragg term is nonzero there
+    hkl = G / 3.0
+    org = np.array([[0, 1, 2, 0], [1, 0, 0, 0], [1, 2, 2, 1], [0, 0, 0, 0]], dtype=np.int32)
+    got = noise.subbox_intensity(m, "disp", mode, 3, hkl, org)
+    want = core.displacive_intensity_direct(m, hkl, mode)
+    np.testing.assert_allclose(got, want, rtol=1e-10, atol=1e-12 * want.max())
+
+
+def test_subbox_origin_sets_average_linearly():
+    """The random-origin estimate is the mean of one-origin estimates, and the list of every
+    lattice point of every supercell gives the every-lattice-point variant."""
+    m = syn.small_case(syn.SPIN, cells=(3, 2, 4), nsite=2, nmodels=2, seed=64)
+    rng = np.random.default_rng(7)
+    hkl = rng.uniform(-1.0, 1.0, (4, 3))
+    org = syn.random_origins(rng, m.nmodels, m.cells, 4)
+    many = noise.subbox_intensity(m, "spin", core.DIFFUSE, 2, hkl, org)
+    ones = [noise.subbox_intensity(m, "spin", core.DIFFUSE, 2, hkl, org[i:i + 1]) for i in range(4)]
+    np.testing.assert_allclose(many, np.mean(ones, axis=0), rtol=1e-12)
+    np.testing.assert_allclose(noise.subbox_intensity(m, "spin", core.TOTAL, 2, hkl, noise.all_origins(m)),
+                               noise.subbox_intensity(m, "spin", core.TOTAL, 2, hkl), rtol=1e-12)
+    cov = syn.covering_origins(rng, m.nmodels, m.cells, 2)
+    for mm in range(m.nmodels):
+        hit = np.zeros(m.cells, dtype=bool)
+        for row in cov[cov[:, 0] == mm]:
+            idx = [np.mod(row[1 + a] + np.arange(2), m.cells[a]) for a in range(3)]
+            hit[np.ix_(*idx)] = True
+        assert hit.all()
+
+
+# ----------------------------------------------------------------------------------------------
+# Debye-Waller factor and the magnetic + displacive coupling (Eqs. dw, mag_sf)
+# ----------------------------------------------------------------------------------------------
+
+def test_debye_waller_closed_forms():
+    """T_mu(Q): 1 without displacements; cos(Q.u0) for a site shifted rigidly by u0 (the even
+    part of exp(i Q.u0)); exp(-sigma^2 |Q|^2 / 2) for isotropic Gaussian displacements, within
+    the sampling error of 2 x 12^3 atoms per site; |T| <= 1."""
+    m = syn.pyrochlore_mag_disp(cells=(12, 12, 12), sigma=0.06, nsite=3, nmodels=2, seed=65)
+    rng = np.random.default_rng(8)
+    hkl = rng.uniform(-5.0, 5.0, (40, 3))
+    Q = core.q_cart(hkl, m.lattice)
+    T = core.debye_waller(m, hkl)
+    assert np.all(np.abs(T) <= 1.0 + 1e-12)
+    gauss = np.exp(-0.5 * 0.06 ** 2 * np.sum(Q * Q, axis=1))
+    nsample = m.nmodels * m.ncell
+    assert np.max(np.abs(T - gauss[:, None])) < 5.0 * math.sqrt(0.5 / nsample)
+    u0 = np.array([[0.2, -0.1, 0.05], [0.0, 0.3, 0.0], [-0.15, 0.0, 0.25]])
+    m.disp = np.broadcast_to(u0[None, :, None, None, None, :], m.disp.shape).astype(np.float32)
+    np.testing.assert_allclose(core.debye_waller(m, hkl), np.cos(Q @ m.disp[0, :, 0, 0, 0].astype(np.float64).T),
+                               rtol=1e-12, atol=1e-14)
+    m.disp = np.zeros_like(m.disp)
+    np.testing.assert_array_equal(core.debye_waller(m, hkl), 1.0)
+
+
+def test_magnetic_debye_waller_coupling():
+    """Eq. mag_sf with T_mu: without displacements T = 1 and the result is the uncoupled one;
+    with one site shifted rigidly by u0 the intensity is cos^2(Q.u0) times the uncoupled one
+    at any Q; and the FFT method with T_mu per voxel equals the direct sum at the Bragg
+    positions of the supercell (TOTAL and DIFFUSE)."""
+    m = syn.pyrochlore_mag_disp(cells=(3, 4, 3), sigma=0.08, nsite=1, nmodels=2, seed=66)
+    rng = np.random.default_rng(9)
+    hkl = rng.uniform(-2.0, 2.0, (9, 3))
+    base = core.magnetic_intensity_direct(m, hkl, core.TOTAL)
+    u0 = np.array([0.13, 0.04, -0.09])
+    keep = m.disp
+    m.disp = np.zeros_like(keep)
+    np.testing.assert_allclose(core.magnetic_intensity_direct(m, hkl, core.TOTAL, dw=True), base, rtol=1e-13)
+    m.disp[:] = u0
+    qu = core.q_cart(hkl, m.lattice) @ m.disp[0, 0, 0, 0, 0].astype(np.float64)
+    np.testing.assert_allclose(core.magnetic_intensity_direct(m, hkl, core.TOTAL, dw=True),
+                               np.cos(qu) ** 2 * base, rtol=1e-12)
+    m3 = syn.pyrochlore_mag_disp(cells=(3, 4, 3), sigma=0.08, nsite=3, nmodels=2, seed=66)
+    G = rng.integers(-7, 8, (30, 3))
+    G[0] = (3, -4, 6)
+    hk = G / np.asarray(m3.cells, dtype=float)
+    for mode in (core.TOTAL, core.DIFFUSE):
+        d = core.magnetic_intensity_direct(m3, hk, mode, dw=True)
+        f = core.magnetic_intensity_fft(m3, G, mode, dw=True)
+        np.testing.assert_allclose(f, d, rtol=1e-10, atol=1e-12 * d.max())
+        assert not np.allclose(d, core.magnetic_intensity_direct(m3, hk, mode), rtol=1e-3)
+
+
 # ----------------------------------------------------------------------------------------------
 # gradient
 # ----------------------------------------------------------------------------------------------
