@@ -548,6 +548,49 @@ def run_rows(dev):
                                             "occupancy 20^3, Lanczos m = 2, FP32 (the paper's plane geometry)",
                                 "ms": ms, "stages_ms": st, "points_per_s": hkl.shape[0] / (ms / 1e3)}
     lp.close()
+
+    # sub-boxes by direct summation (S6b'): random origins covering the fcc 32^3 displacive
+    # supercell, n_sb = 5, exact exp(i Q.u), (h h l) plane 201 x 201, DIFFUSE
+    md = syn.displacive_fcc(cells=(32, 32, 32), sigma=0.1, seed=5)
+    ld = ds.Model(ctx, md.lattice, md.sites, md.cells, 1, md.scat_len, md.ff_kind, md.ff_coef)
+    ld.upload_displacements(np.ascontiguousarray(md.disp))
+    org = syn.covering_origins(np.random.default_rng(7), 1, md.cells, 5)
+    u, v = np.meshgrid(np.linspace(-5.0, 5.0, 201), np.linspace(-5.0, 5.0, 201), indexing="ij")
+    hkl = torch.from_numpy(np.stack([u.ravel(), u.ravel(), v.ravel()], axis=1)).to(dev)
+    pts = torch.empty(hkl.shape[0], dtype=torch.float32, device=dev)
+    ms, st = timed(lambda: ld.subbox_points(hkl, org, out=pts, disorder=ds.DS_DISP, mode=ds.DS_DIFFUSE,
+                                            precision=ds.DS_FP32, subbox_n=5), reps=2)
+    terms = float(hkl.shape[0]) * org.shape[0] * 125 * md.nsite
+    sb = st.get("subbox_dft", float("nan"))
+    mufu = 152 * 16 * 2.07e9 / 2.0   # __sincosf = two SFU operations; 16 SFU lanes per SM per clock
+    rows["subbox_random_disp_fcc32_plane"] = {
+        "workload": "fcc 32^3 displacive (u ~ N(0, 0.1^2)), %d random origins covering every cell, n_sb = 5, "
+                    "(h h l) plane 201 x 201 |h|, |l| <= 5, DIFFUSE, FP32" % org.shape[0],
+        "ms": ms, "stages_ms": st, "points_per_s": hkl.shape[0] / (ms / 1e3),
+        "roofline": {"bound": "alu", "achieved": terms / (sb / 1e3) / 1e12, "peak": mufu / 1e12,
+                     "unit": "Tterm/s", "frac": terms / (sb / 1e3) / mufu,
+                     "note": "one exp(i Q.u) (two SFU operations) per atom, box and point"}}
+    ld.close()
+
+    # magnetic + displacive coupling through T_mu(G) (Eq. mag_sf): pyrochlore 20^3, |hkl| <= 2
+    mm = syn.pyrochlore_mag_disp(cells=(20, 20, 20), hmax=2.0)
+    lmg = ds.Model(ctx, mm.lattice, mm.sites, mm.cells, 1, mm.scat_len, mm.ff_kind, mm.ff_coef)
+    lmg.upload_spins(np.ascontiguousarray(mm.spins))
+    lmg.upload_displacements(np.ascontiguousarray(mm.disp))
+    q = (mm.qgrid.h0, mm.qgrid.step, mm.qgrid.count)
+    out = torch.empty(mm.qgrid.count, dtype=torch.float32, device=dev)
+    ms, st = timed(lambda: lmg.intensity(q, out=out, disorder=ds.DS_SPIN, mode=ds.DS_TOTAL, precision=ds.DS_FP32,
+                                         dw_coupling=1), reps=2)
+    dwms = st.get("debye_waller", float("nan"))
+    cos_terms = float(mm.qgrid.nvox) * mm.nsite * mm.ncell
+    rows["mag_dw_pyrochlore20"] = {
+        "workload": "magnetic pyrochlore 20^3 with u ~ N(0, 0.05^2), |hkl| <= 2 step 1/20 (%d^3 voxels), "
+                    "T_mu(G) per voxel and site, FP32" % mm.qgrid.count[0],
+        "ms": ms, "stages_ms": st, "voxels_per_s": mm.qgrid.nvox / (ms / 1e3),
+        "roofline": {"bound": "alu", "achieved": cos_terms / (dwms / 1e3) / 1e12, "peak": 2.0 * mufu / 1e12,
+                     "unit": "Tterm/s", "frac": cos_terms / (dwms / 1e3) / (2.0 * mufu),
+                     "note": "Debye-Waller kernel: one cos (one SFU operation) per voxel, site and lattice point"}}
+    lmg.close()
     ctx.close()
     return rows
 

@@ -94,6 +94,11 @@ typedef struct {
                            grid, from x_H = min(max_zone |Q| * max_j |u_j|, x_max), so that the
                            same remainder bound holds at every voxel (|Q.u| <= |Q||u|); 0 = one
                            order for the whole grid.  Not accepted by ds_backward. */
+    int dw_coupling;    /* magnetic (DS_SPIN) only: 1 = multiply each site's term of Eq. mag_sf by
+                           the Debye-Waller factor T_mu(G) of the uploaded displacements (Eq. dw,
+                           even part: the mean over lattice points and supercells of cos(G.u)),
+                           the only coupling of moments and displacements the paper keeps;
+                           0 = T = 1.  Not with DS_SMOOTH_SUBBOX, not accepted by ds_backward. */
 } ds_opts;
 
 typedef struct {
@@ -164,6 +169,35 @@ ds_status ds_request_intensity(ds_model *model, const ds_qgrid *grid, const ds_o
  * (box larger than the budget), DS_ERR_UNSUPPORTED, the errors of ds_request_intensity. */
 ds_status ds_request_points(ds_model *model, const double *hkl, int64_t npts, int hkl_is_device, const ds_opts *opts,
                             void *out, int out_is_device, void *stream, ds_result_info *info);
+
+/* Method of sub-boxes by direct summation (Section V A) at npts arbitrary wavevectors hkl
+ * ([npts][3] r.l.u., host or device).  Each origin (m, o1, o2, o3) -- lattice point o of
+ * supercell m -- is the corner of a box of n_sb^3 cells o + d, d in [0, n_sb)^3, with open
+ * boundaries: its atoms sit at o + d + r_mu (+ u) and carry the data of the wrapped cells
+ * (o + d) mod n.  I(Q) = sum_o |F_o(Q)|^2 / (norigin nsite n_sb^3) (magnetic: C |F_o,perp|^2).
+ * Amplitudes: DS_OCC b delta (DIFFUSE b (delta - c_mu)); DS_SPIN b M (DIFFUSE M - <M>_mu);
+ * DS_DISP b delta exp(i Q.u) with the exact exponential (delta = 1 without occupancies; DIFFUSE
+ * subtracts b <delta cos(Q.u)>_mu, the Debye-Waller factor of ds_debye_waller, so that n_sb = n
+ * at a supercell Bragg position gives F - <F> of Eq. bragg_sf_disp).  origins: host int32
+ * [norigin][4] (the random-origin variant: origins drawn by the caller), or NULL with
+ * norigin = 0 for every lattice point of every supercell.  Options read: disorder, mode,
+ * precision, subbox_n (1 <= n_sb <= n_alpha; the paper keeps n_sb <= n_alpha/2 to avoid
+ * periodic images).  The work is O(npts norigin nsite n_sb^3).  out: npts values of the
+ * precision's type, host or device; the call synchronises `stream` before it returns.
+ * Errors: DS_ERR_ARG (origins outside the supercells, non-finite points, n_sb), DS_ERR_STATE,
+ * DS_ERR_OOM, DS_ERR_ADMISSION, DS_ERR_CUDA. */
+ds_status ds_request_subbox_points(ds_model *model, const int32_t *origins, int64_t norigin, const double *hkl,
+                                   int64_t npts, int hkl_is_device, const ds_opts *opts, void *out, int out_is_device,
+                                   void *stream, ds_result_info *info);
+
+/* Debye-Waller factor T_mu(Q) of Eq. dw at npts wavevectors hkl ([npts][3] r.l.u., host or
+ * device): out[p][mu] = mean over lattice points and supercells of w cos(Q.u_{R,mu}), the even
+ * part of Eq. dw (the odd orders of Q.u average to zero over the ensemble); w = the occupancy
+ * delta when occupancy_weights != 0 and occupancies are uploaded, else 1.  precision DS_FP32 or
+ * DS_FP64 (type of out); synchronises `stream`.  Errors: DS_ERR_ARG, DS_ERR_STATE (no
+ * displacements), DS_ERR_OOM, DS_ERR_CUDA. */
+ds_status ds_debye_waller(ds_model *model, const double *hkl, int64_t npts, int hkl_is_device, int precision,
+                          int occupancy_weights, void *out, int out_is_device, void *stream);
 
 /* Serving: queue a request (device `out`, kept valid until completion).  The call validates
  * the request, chooses the Taylor order (displacive, reading x_max back on the context's own

@@ -181,6 +181,46 @@ class Model:
                                                   _stream_of(out, stream), C.byref(info)))
         return out, info.as_dict()
 
+    def subbox_points(self, hkl, origins=None, out=None, stream=None, **opts):
+        """Sub-box average at arbitrary points hkl [npts, 3] (ds_request_subbox_points): boxes of
+        subbox_n^3 cells at `origins` (int32 [norigin, 4] rows (model, o1, o2, o3), e.g. drawn
+        at random) or, with origins=None, at every lattice point of every supercell.
+        Returns (out, info dict)."""
+        opts.setdefault("smoothing", DS_SMOOTH_SUBBOX)
+        o = make_opts(**opts)
+        dt = np.float64 if o.precision == DS_FP64 else np.float32
+        if not _is_torch(hkl):
+            hkl = np.ascontiguousarray(hkl, dtype=np.float64).reshape(-1, 3)
+        ph, hdev = _ptr(hkl, np.float64)
+        npts = int(hkl.shape[0]) if len(hkl.shape) == 2 else int(np.prod(hkl.shape)) // 3
+        porg, norg = None, 0
+        if origins is not None:
+            origins = np.ascontiguousarray(origins, dtype=np.int32).reshape(-1, 4)
+            porg, norg = origins.ctypes.data_as(C.c_void_p), int(origins.shape[0])
+        if out is None:
+            out = np.empty(npts, dtype=dt)
+        po, odev = _ptr(out, dt)
+        info = ds_result_info()
+        self.ctx.check(self.lib.ds_request_subbox_points(self.h, porg, C.c_int64(norg), ph, C.c_int64(npts), hdev,
+                                                         C.byref(o), po, odev, _stream_of(out, stream),
+                                                         C.byref(info)))
+        return out, info.as_dict()
+
+    def debye_waller(self, hkl, precision=DS_FP64, occupancy_weights=False, out=None, stream=None):
+        """T_mu(Q) of the uploaded displacements at points hkl [npts, 3]: [npts, nsite]
+        (ds_debye_waller)."""
+        dt = np.float64 if precision == DS_FP64 else np.float32
+        if not _is_torch(hkl):
+            hkl = np.ascontiguousarray(hkl, dtype=np.float64).reshape(-1, 3)
+        ph, hdev = _ptr(hkl, np.float64)
+        npts = int(hkl.shape[0]) if len(hkl.shape) == 2 else int(np.prod(hkl.shape)) // 3
+        if out is None:
+            out = np.empty((npts, self.nsite), dtype=dt)
+        po, odev = _ptr(out, dt)
+        self.ctx.check(self.lib.ds_debye_waller(self.h, ph, C.c_int64(npts), hdev, int(precision),
+                                                int(bool(occupancy_weights)), po, odev, _stream_of(out, stream)))
+        return out
+
     def backward(self, qgrid, dL_dI, grad=None, stream=None, **opts):
         """dL/du (displacive) or dL/dM (magnetic) for a given dL/dI on `qgrid`."""
         q = make_qgrid(*qgrid)

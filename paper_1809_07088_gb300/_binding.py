@@ -31,7 +31,7 @@ class ds_opts(C.Structure):
     _fields_ = [("disorder", C.c_int), ("mode", C.c_int), ("precision", C.c_int),
                 ("taylor_order", C.c_int), ("taylor_eps", C.c_double), ("smoothing", C.c_int),
                 ("lanczos_m", C.c_int), ("lanczos_mprime", C.c_int), ("subbox_n", C.c_int),
-                ("taylor_zonal", C.c_int)]
+                ("taylor_zonal", C.c_int), ("dw_coupling", C.c_int)]
 
 
 class ds_result_info(C.Structure):
@@ -64,6 +64,9 @@ SIGNATURES = {
                                   C.POINTER(ds_result_info)]),
     "ds_request_points": (st, [vp, vp, C.c_int64, C.c_int, C.POINTER(ds_opts), vp, C.c_int, vp,
                                C.POINTER(ds_result_info)]),
+    "ds_request_subbox_points": (st, [vp, vp, C.c_int64, vp, C.c_int64, C.c_int, C.POINTER(ds_opts), vp,
+                                      C.c_int, vp, C.POINTER(ds_result_info)]),
+    "ds_debye_waller": (st, [vp, vp, C.c_int64, C.c_int, C.c_int, C.c_int, vp, C.c_int, vp]),
     "ds_submit": (st, [vp, C.POINTER(ds_qgrid), C.POINTER(ds_opts), vp, C.POINTER(C.c_uint64)]),
     "ds_poll": (st, [vp, C.c_uint64, C.POINTER(ds_result_info)]),
     "ds_wait": (st, [vp, C.c_uint64, C.c_double, C.POINTER(ds_result_info)]),
@@ -117,11 +120,12 @@ def make_qgrid(h0, step, count) -> ds_qgrid:
 
 def make_opts(disorder, mode=DS_DIFFUSE, precision=DS_FP32, taylor_order=-1, taylor_eps=1e-8,
               smoothing=DS_SMOOTH_NONE, lanczos_m=2, lanczos_mprime=2, subbox_n=1,
-              taylor_zonal=0) -> ds_opts:
+              taylor_zonal=0, dw_coupling=0) -> ds_opts:
     o = ds_opts()
     o.disorder, o.mode, o.precision = int(disorder), int(mode), int(precision)
     o.taylor_order, o.taylor_eps = int(taylor_order), float(taylor_eps)
     o.smoothing, o.lanczos_m, o.lanczos_mprime, o.subbox_n = int(smoothing), int(lanczos_m), \
         int(lanczos_mprime), int(subbox_n)
     o.taylor_zonal = int(taylor_zonal)
+    o.dw_coupling = int(dw_coupling)
     return o

@@ -458,6 +458,7 @@ extern "C" ds_status ds_backward(ds_model *M, const ds_qgrid *q, const ds_opts *
     if (o->mode != DS_TOTAL) return ds_fail(ctx, DS_ERR_UNSUPPORTED, "the adjoint is defined for DS_TOTAL mode");
     if (o->smoothing != DS_SMOOTH_NONE) return ds_fail(ctx, DS_ERR_UNSUPPORTED, "the adjoint takes no smoothing");
     if (o->taylor_zonal) return ds_fail(ctx, DS_ERR_UNSUPPORTED, "the adjoint uses one Taylor order for the grid");
+    if (o->dw_coupling) return ds_fail(ctx, DS_ERR_UNSUPPORTED, "the adjoint does not differentiate the Debye-Waller coupling");
     if (cudaSetDevice(ctx->device) != cudaSuccess) return ds_fail(ctx, DS_ERR_CUDA, "cudaSetDevice");
     cudaStream_t st = (cudaStream_t)stream;
     if (o->precision == DS_FP64) return backward_entry<double>(M, q, o, dLdI, grad, is_device, st);

@@ -636,6 +636,14 @@ ds_status check_request(ds_model *M, const ds_qgrid *q, const ds_opts *o) {
         return ds_fail(ctx, DS_ERR_ARG, "taylor_eps must be in (0, 1) when taylor_order < 0");
     if (o->disorder == DS_DISP && o->taylor_order > 60) return ds_fail(ctx, DS_ERR_UNSUPPORTED, "taylor_order > 60");
     if (o->taylor_zonal != 0 && o->taylor_zonal != 1) return ds_fail(ctx, DS_ERR_ARG, "taylor_zonal must be 0 or 1");
+    if (o->dw_coupling != 0 && o->dw_coupling != 1) return ds_fail(ctx, DS_ERR_ARG, "dw_coupling must be 0 or 1");
+    if (o->dw_coupling) {
+        if (o->disorder != DS_SPIN)
+            return ds_fail(ctx, DS_ERR_UNSUPPORTED, "dw_coupling applies to magnetic requests (Eq. mag_sf)");
+        if (!M->has_disp) return ds_fail(ctx, DS_ERR_STATE, "dw_coupling needs uploaded displacements");
+        if (o->smoothing == DS_SMOOTH_SUBBOX)
+            return ds_fail(ctx, DS_ERR_UNSUPPORTED, "dw_coupling is not combined with sub-box averaging");
+    }
     if (o->disorder != DS_DISP && M->nsite > 32 && o->disorder == DS_OCC)
         return ds_fail(ctx, DS_ERR_UNSUPPORTED, "occupancy recombination handles up to 32 sites");
     if (o->disorder == DS_SPIN && M->nsite > 16)
@@ -767,10 +775,9 @@ size_t request_footprint(const ds_model *M, const ds_qgrid *q, const ds_opts *o,
     }
     const size_t fb = std::max<size_t>(1, std::min<size_t>(nf, (512ull << 20) / (ce * g.ncell_h)));
     bytes += (nf + fb) * g.ncell_h * ce;
-    if (lanczos_like(o)) {
-        const int h = lanczos_halo(o->lanczos_m, o->lanczos_mprime);
-        bytes += 3 * (cnt[0] + 2 * h) * (cnt[1] + 2 * h) * (cnt[2] + 2 * h) * es;
-    }
+    const int hl = lanczos_like(o) ? lanczos_halo(o->lanczos_m, o->lanczos_mprime) : 0;
+    if (lanczos_like(o)) bytes += 3 * (cnt[0] + 2 * hl) * (cnt[1] + 2 * hl) * (cnt[2] + 2 * hl) * es;
+    if (o->dw_coupling) bytes += nsite * (cnt[0] + 2 * hl) * (cnt[1] + 2 * hl) * (cnt[2] + 2 * hl) * es;
     return bytes;
 }
 
@@ -1005,6 +1012,15 @@ ds_status plan_and_run(ds_model *M, const ds_qgrid *q, const ds_opts *o, T *d_ou
     // recombination over the requested voxels (+ Bragg term)
     if (keep && keep->Fout) {
         p.Fout = keep->Fout;
+        p.force_plain = 1;
+    }
+    if (o->disorder == DS_SPIN && o->dw_coupling) {
+        // T_mu(G) per voxel and site breaks the sharing of site sums across zones: plain kernel
+        T *dw = (T *)ws.get(sizeof(T) * (size_t)nsite * ecnt[0] * ecnt[1] * ecnt[2]);
+        if (ws.failed) return ds_fail(ctx, DS_ERR_OOM, "device allocation failed (Debye-Waller factors)");
+        ProfScope ps(ctx, "debye_waller", st);
+        debye_waller_grid<T>(M, eg0, ecnt, dw, st);
+        p.dw = dw;
         p.force_plain = 1;
     }
     if (o->disorder == DS_DISP) {

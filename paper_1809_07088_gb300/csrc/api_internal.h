@@ -160,6 +160,8 @@ bool lanczos_like(const ds_opts *o);
 double sphere_cutoff_radius(const ds_model *M, int m, int mprime);
 double sphere_profile(double x);
 void sphere_stencil_weights(const ds_model *M, int m, int mprime, int h, std::vector<double> &w);
+// T_mu(G) of Eq. dw on the grid g0 + [0, cnt) of supercell indices, [site][voxel] (subbox_dft.cu)
+template <typename T> void debye_waller_grid(const ds_model *M, const int g0[3], const int cnt[3], T *out, cudaStream_t st);
 // sub-box averaging (subbox.cu)
 template <typename T>
 ds_status subbox_run(ds_model *M, const ds_qgrid *q, const ds_opts *o, T *d_out, cudaStream_t st, Scratch &ws,

@@ -131,6 +131,7 @@ template <typename T> struct RecombParams {
     c_t<T> *Fout;                       // optional: F per voxel [model][voxel][ncomp] (adjoint)
     int force_plain;                    // use the per-site (ungrouped) recombination
     int dres[3];                        // residue classes of zones per axis (0: per-zone kernels)
+    const T *dw;                        // optional: Debye-Waller factor T_mu(G) [site][voxel] (magnetic)
     int *err;
 };
 

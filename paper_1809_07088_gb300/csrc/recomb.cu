@@ -263,7 +263,11 @@ __global__ void __launch_bounds__(256, MINB)
         if (G1 < gm.g0[0] || G1 >= gm.g0[0] + gm.cnt[0]) continue;
         if (G2 < gm.g0[1] || G2 >= gm.g0[1] + gm.cnt[1]) continue;
         const C *Prow = Ptab + (size_t)j12 * nH3 * nsite;
-        T *orow = p.out + ((size_t)(G1 - gm.g0[0]) * gm.cnt[1] + (G2 - gm.g0[1])) * gm.cnt[2] - gm.g0[2];
+        const long long row0 = ((long long)(G1 - gm.g0[0]) * gm.cnt[1] + (G2 - gm.g0[1])) * gm.cnt[2] - gm.g0[2];
+        T *orow = p.out + row0;
+        // Debye-Waller factor T_mu(G) of this row (magnetic + displacive coupling, Eq. mag_sf)
+        const T *dwrow = p.dw ? p.dw + row0 : nullptr;
+        const long long dw_site_stride = (long long)gm.cnt[0] * gm.cnt[1] * gm.cnt[2];
         // Cartesian Q = (G1/n1) a* + (G2/n2) b* + (G3/n3) c*, the G3 part added per voxel
         T Q12[3], c3[3];
 #pragma unroll
@@ -292,7 +296,10 @@ __global__ void __launch_bounds__(256, MINB)
                 if (s < nsite) {
 #pragma unroll
                     for (int v = 0; v < VPI; ++v) {
-                        const C ps = Prow[(size_t)min(h3 + v, h3hi) * nsite + s];
+                        C ps = Prow[(size_t)min(h3 + v, h3hi) * nsite + s];
+                        if (dwrow)
+                            ps = cscale(ps, dwrow[(long long)p.site_of[s] * dw_site_stride +
+                                                  (long long)(g.n[2] * (gm.Hmin[2] + min(h3 + v, h3hi)) + k3)]);
                         if (ONECLS) {
 #pragma unroll
                             for (int c = 0; c < NC; ++c) cfma(F[v][c], ps, Y[s][c]);

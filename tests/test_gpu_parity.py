@@ -449,6 +449,162 @@ def test_subbox_residue_classes_against_brute_force(ctx, disorder, kind, ff, mod
 
 
 # ----------------------------------------------------------------------------------------------
+# sub-boxes by direct summation over origins (Section V A)
+# ----------------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("prec,tag", PREC)
+@pytest.mark.parametrize("disorder,kind", [("occ", 0), ("spin", 1), ("disp", 2)])
+@pytest.mark.parametrize("mode", [0, 1])
+def test_subbox_points_random_origins(ctx, prec, tag, disorder, kind, mode):
+    """Random-origin sub-boxes (the original variant of Section V A) at arbitrary Q on a
+    triclinic cell with mixed form factors, 301 points (three blocks and a ragged tail), against
+    the oracle's literal loop over the same origins; displacive boxes use exact exponentials."""
+    m = syn.small_case(kind, cells=(6, 5, 7), nsite=3, nmodels=2, seed=150 + kind, sigma=0.1)
+    lm = to_library(ctx, m)
+    rng = np.random.default_rng(20 + kind)
+    hkl = rng.uniform(-2.0, 2.0, (301, 3))
+    org = syn.random_origins(rng, m.nmodels, m.cells, 9)
+    got, info = lm.subbox_points(hkl, org, disorder=kind, mode=mode, precision=prec, subbox_n=3)
+    assert info["nvox"] == hkl.shape[0]
+    want = noise.subbox_intensity(m, disorder, mode, 3, hkl, org)
+    assert rel_err_of_peak(got, want) < TOL[tag]
+
+
+@pytest.mark.parametrize("disorder,kind", [("occ", 0), ("spin", 1)])
+def test_subbox_points_every_origin_equals_pair_route(ctx, disorder, kind):
+    """Every lattice point an origin, at the supercell Bragg positions: the direct sum over boxes
+    equals the GPU's pair-spectrum route (DS_SMOOTH_SUBBOX on the grid) and the oracle."""
+    m = syn.small_case(kind, cells=(6, 7, 6), nsite=3, nmodels=2, seed=160 + kind)
+    q = syn.QGrid(tuple(-1.0 - 1.0 / n for n in m.cells), tuple(1.0 / n for n in m.cells),
+                  tuple(n + 3 for n in m.cells))
+    lm = to_library(ctx, m)
+    hkl = q.g_index(m.cells) / np.array(m.cells, dtype=float)
+    want = noise.subbox_intensity(m, disorder, 1, 2, hkl)
+    for prec, tag in PREC:
+        grid, _ = lm.intensity(qgrid_tuple(q), disorder=kind, mode=1, precision=prec, smoothing=2, subbox_n=2)
+        pts, _ = lm.subbox_points(hkl, None, disorder=kind, mode=1, precision=prec, subbox_n=2)
+        assert rel_err_of_peak(pts, grid.reshape(-1)) < TOL[tag]
+        assert rel_err_of_peak(pts, want) < TOL[tag]
+
+
+@pytest.mark.parametrize("prec,tag", PREC)
+def test_subbox_points_displacive_every_origin_and_whole_box(ctx, prec, tag):
+    """Displacive sub-boxes, every origin, against the oracle; and n_sb = n (one box spanning the
+    supercell) at Bragg positions against the exact direct sum F - <F> (no Taylor expansion on
+    either side), device points and device output."""
+    import torch
+    m = syn.small_case(syn.DISP, cells=(4, 3, 5), nsite=2, nmodels=2, seed=170, sigma=0.15)
+    lm = to_library(ctx, m)
+    rng = np.random.default_rng(31)
+    hkl = np.concatenate([rng.uniform(-2.5, 2.5, (61, 3)), [[1.0, -1.0, 2.0], [0.0, 0.0, 0.0]]])
+    for mode in (0, 1):
+        got, _ = lm.subbox_points(hkl, None, disorder=2, mode=mode, precision=prec, subbox_n=2)
+        assert rel_err_of_peak(got, noise.subbox_intensity(m, "disp", mode, 2, hkl)) < TOL[tag]
+    hb = rng.uniform(-3.0, 3.0, (40, 3))
+    org = np.array([[0, 1, 2, 3], [1, 0, 0, 0], [0, 3, 0, 1], [1, 2, 1, 4]], dtype=np.int32)
+    dt = torch.float64 if prec == 0 else torch.float32
+    out = torch.empty(hb.shape[0], dtype=dt, device="cuda")
+    for mode in (0, 1):
+        lm.subbox_points(torch.from_numpy(hb).cuda(), org, out=out, disorder=2, mode=mode, precision=prec,
+                         subbox_n=3)
+        torch.cuda.synchronize()
+        assert rel_err_of_peak(out.cpu().numpy(), noise.subbox_intensity(m, "disp", mode, 3, hb, org)) < TOL[tag]
+    whole = syn.small_case(syn.DISP, cells=(3, 3, 3), nsite=2, nmodels=2, seed=171, sigma=0.15)
+    lw = to_library(ctx, whole)
+    G3 = rng.integers(-7, 8, (50, 3))
+    G3[0] = (3, 0, -3)
+    h3 = G3 / 3.0
+    org3 = np.array([[0, 1, 2, 0], [1, 2, 1, 1], [1, 0, 0, 0], [0, 0, 0, 1]], dtype=np.int32)  # two per supercell
+    for mode in (0, 1):
+        got, _ = lw.subbox_points(h3, org3, disorder=2, mode=mode, precision=prec, subbox_n=3)
+        want = core.displacive_intensity_direct(whole, h3, mode)
+        assert rel_err_of_peak(got, want) < TOL[tag]
+
+
+def test_subbox_points_errors(ctx):
+    import paper_1809_07088_gb300 as ds
+    m = syn.small_case(syn.OCC, cells=(4, 4, 4), nsite=2, nmodels=1, seed=172)
+    lm = to_library(ctx, m)
+    hkl = np.zeros((3, 3))
+    with pytest.raises(ds.DSError):
+        lm.subbox_points(hkl, np.array([[1, 0, 0, 0]], dtype=np.int32), disorder=0, subbox_n=2)  # model 1 of 1
+    with pytest.raises(ds.DSError):
+        lm.subbox_points(hkl, np.array([[0, 4, 0, 0]], dtype=np.int32), disorder=0, subbox_n=2)
+    with pytest.raises(ds.DSError):
+        lm.subbox_points(hkl, None, disorder=0, subbox_n=0)
+    with pytest.raises(ds.DSError):
+        lm.subbox_points(hkl, None, disorder=0, subbox_n=5)        # n_sb > n_alpha
+    with pytest.raises(ds.DSError):
+        lm.subbox_points(hkl, None, disorder=1, subbox_n=2)        # no spins uploaded
+    with pytest.raises(ds.DSError):
+        lm.subbox_points(np.array([[np.inf, 0.0, 0.0]]), None, disorder=0, subbox_n=2)
+    out, info = lm.subbox_points(np.zeros((0, 3)), None, disorder=0, subbox_n=2)
+    assert out.shape == (0,) and info["nvox"] == 0
+
+
+# ----------------------------------------------------------------------------------------------
+# Debye-Waller factor and the magnetic + displacive coupling (Eqs. dw, mag_sf)
+# ----------------------------------------------------------------------------------------------
+
+def _mag_disp_case(seed, cells=(5, 4, 6), nsite=3):
+    m = syn.small_case(syn.SPIN, cells=cells, nsite=nsite, nmodels=2, seed=seed)
+    m.disp = syn.gaussian_displacements(np.random.default_rng(seed + 1), m.nmodels, m.nsite, m.cells, 0.1)
+    return m
+
+
+@pytest.mark.parametrize("prec,tol", [(0, 1e-12), (1, 2e-6)])
+def test_debye_waller_points(ctx, prec, tol):
+    """T_mu(Q) (Eq. dw, even part) at 257 arbitrary points, unweighted and weighted by the
+    occupancies, against the oracle's direct mean (absolute error; |T| <= 1)."""
+    m = syn.small_case(syn.DISP, cells=(6, 5, 4), nsite=3, nmodels=2, seed=180, sigma=0.12)
+    lm = to_library(ctx, m)
+    hkl = np.random.default_rng(41).uniform(-4.0, 4.0, (257, 3))
+    for occw in (False, True):
+        got = lm.debye_waller(hkl, precision=prec, occupancy_weights=occw)
+        want = core.debye_waller(m, hkl, occupancy=occw)
+        assert got.shape == want.shape
+        assert np.max(np.abs(got - want)) < tol
+
+
+@pytest.mark.parametrize("prec,tag", PREC)
+@pytest.mark.parametrize("mode", [0, 1])
+def test_magnetic_debye_waller_coupling(ctx, prec, tag, mode):
+    """Eq. mag_sf with T_mu(G) of the uploaded displacements (dw_coupling = 1) on the grid of
+    Bragg positions (triclinic, Q = 0 included) against the oracle's FFT method with the same
+    factor; and at arbitrary points through the Lanczos route."""
+    m = _mag_disp_case(190)
+    lm = to_library(ctx, m)
+    got, _ = lm.intensity(qgrid_tuple(m.qgrid), disorder=1, mode=mode, precision=prec, dw_coupling=1)
+    want = core.magnetic_intensity_fft(m, _G(m), mode, dw=True)
+    assert rel_err_of_peak(got, want) < TOL[tag]
+    plain, _ = lm.intensity(qgrid_tuple(m.qgrid), disorder=1, mode=mode, precision=prec)
+    assert rel_err_of_peak(plain, want) > 1e-3
+    hkl = np.random.default_rng(43).uniform(-0.9, 0.9, (90, 3))
+    gp, _ = lm.intensity_points(hkl, disorder=1, mode=mode, precision=prec, dw_coupling=1)
+    wp = noise.lanczos_resample(lambda G: core.magnetic_intensity_fft(m, G, mode, dw=True),
+                                hkl * np.array(m.cells), 2, 2)
+    assert rel_err_of_peak(gp, wp) < TOL[tag]
+
+
+def test_magnetic_debye_waller_errors(ctx):
+    import paper_1809_07088_gb300 as ds
+    m = _mag_disp_case(191, cells=(4, 4, 4), nsite=2)
+    lm = to_library(ctx, m)
+    q = qgrid_tuple(m.qgrid)
+    with pytest.raises(ds.DSError):
+        lm.intensity(q, disorder=2, dw_coupling=1)                     # not magnetic
+    with pytest.raises(ds.DSError):
+        lm.intensity(q, disorder=1, dw_coupling=1, smoothing=2, subbox_n=2)
+    with pytest.raises(ds.DSError):
+        lm.intensity(q, disorder=1, dw_coupling=2)
+    with pytest.raises(ds.DSError):
+        lm.backward(q, np.ones(m.qgrid.count, dtype=np.float32), disorder=1, mode=0, dw_coupling=1)
+    nodisp = to_library(ctx, m, with_disp=False)
+    with pytest.raises(ds.DSError):
+        nodisp.intensity(q, disorder=1, dw_coupling=1)
+
+
+# ----------------------------------------------------------------------------------------------
 # adjoint
 # ----------------------------------------------------------------------------------------------
 
