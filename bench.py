@@ -598,7 +598,9 @@ def run_rows(dev):
 def run_profile_workload(name):
     """A small case of one row, run twice, for ncu captures (a few hundred MB on the device):
     taylor = fcc 32^3, 321^3 voxels, P = 12; lanczos = occupancy 32^3 cells, 513^3 voxels,
-    m = 2, m' = 8; subbox = the pyrochlore occupancy volume with n_sb = 5."""
+    m = 2, m' = 8; subbox = the pyrochlore occupancy volume with n_sb = 5; subbox_dft = the
+    random-origin displacive boxes on a 101 x 101 (h h l) plane; dw = the magnetic pyrochlore
+    with T_mu(G), |hkl| <= 1."""
     import ctypes
     import numpy as np
     import torch
@@ -622,20 +624,38 @@ def run_profile_workload(name):
         lm.upload_occupancy(np.ascontiguousarray(m.occ))
         opts = dict(disorder=ds.DS_OCC, mode=ds.DS_DIFFUSE, precision=ds.DS_FP32, smoothing=ds.DS_SMOOTH_LANCZOS,
                     lanczos_m=2, lanczos_mprime=8)
+    elif name == "subbox_dft":
+        m = syn.displacive_fcc(cells=(32, 32, 32), sigma=0.1, seed=5)
+        lm = ds.Model(ctx, m.lattice, m.sites, m.cells, 1, m.scat_len, m.ff_kind, m.ff_coef)
+        lm.upload_displacements(np.ascontiguousarray(m.disp))
+        org = syn.covering_origins(np.random.default_rng(7), 1, m.cells, 5)
+        u, v = np.meshgrid(np.linspace(-5.0, 5.0, 101), np.linspace(-5.0, 5.0, 101), indexing="ij")
+        hkl = torch.from_numpy(np.stack([u.ravel(), u.ravel(), v.ravel()], axis=1)).cuda()
+        pts = torch.empty(hkl.shape[0], dtype=torch.float32, device="cuda")
+        opts = dict(disorder=ds.DS_DISP, mode=ds.DS_DIFFUSE, precision=ds.DS_FP32, subbox_n=5)
+        call = lambda: lm.subbox_points(hkl, org, out=pts, **opts)
+    elif name == "dw":
+        m = syn.pyrochlore_mag_disp(cells=(20, 20, 20), hmax=1.0)
+        lm = ds.Model(ctx, m.lattice, m.sites, m.cells, 1, m.scat_len, m.ff_kind, m.ff_coef)
+        lm.upload_spins(np.ascontiguousarray(m.spins))
+        lm.upload_displacements(np.ascontiguousarray(m.disp))
+        opts = dict(disorder=ds.DS_SPIN, mode=ds.DS_TOTAL, precision=ds.DS_FP32, dw_coupling=1)
     else:
         m = syn.pyrochlore_occ_mag()
         lm = ds.Model(ctx, m.lattice, m.sites, m.cells, 1, m.scat_len, m.ff_kind, m.ff_coef)
         lm.upload_occupancy(np.ascontiguousarray(m.occ))
         opts = dict(disorder=ds.DS_OCC, mode=ds.DS_DIFFUSE, precision=ds.DS_FP32, smoothing=ds.DS_SMOOTH_SUBBOX,
                     subbox_n=5)
-    q = (m.qgrid.h0, m.qgrid.step, m.qgrid.count)
-    out = torch.empty(m.qgrid.count, dtype=torch.float32, device="cuda")
-    lm.intensity(q, out=out, **opts)
+    if name != "subbox_dft":
+        q = (m.qgrid.h0, m.qgrid.step, m.qgrid.count)
+        out = torch.empty(m.qgrid.count, dtype=torch.float32, device="cuda")
+        call = lambda: lm.intensity(q, out=out, **opts)
+    call()
     torch.cuda.synchronize()
     buf = ctypes.create_string_buffer(1 << 16)
     ctx.lib.ds_profile_report(ctx.h, buf, len(buf))
     ctx.lib.ds_profile_enable(ctx.h, 1)
-    lm.intensity(q, out=out, **opts)
+    call()
     torch.cuda.synchronize()
     ctx.check(ctx.lib.ds_profile_report(ctx.h, buf, len(buf)))
     print(json.dumps({"profile_workload": name, "stages": json.loads(buf.value.decode())["stages"]}))
@@ -778,7 +798,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serving", type=int, default=128, help="requests in the serving stream (0 = skip)")
     ap.add_argument("--no-rows", action="store_true", help="skip the per-row measurements")
-    ap.add_argument("--profile-workload", choices=["taylor", "lanczos", "subbox"], default=None,
+    ap.add_argument("--profile-workload", choices=["taylor", "lanczos", "subbox", "subbox_dft", "dw"], default=None,
                     help="run one small row workload twice (for ncu captures) and exit")
     ap.add_argument("--streams", type=int, default=2, choices=[1, 2],
                     help="2: the two volumes of a step on two streams (their kernels overlap)")

@@ -185,7 +185,7 @@ ds_status ds_request_points(ds_model *model, const double *hkl, int64_t npts, in
  * periodic images).  The work is O(npts norigin nsite n_sb^3).  out: npts values of the
  * precision's type, host or device; the call synchronises `stream` before it returns.
  * Errors: DS_ERR_ARG (origins outside the supercells, non-finite points, n_sb), DS_ERR_STATE,
- * DS_ERR_OOM, DS_ERR_ADMISSION, DS_ERR_CUDA. */
+ * DS_ERR_UNSUPPORTED (more than 16 sites), DS_ERR_OOM, DS_ERR_ADMISSION, DS_ERR_CUDA. */
 ds_status ds_request_subbox_points(ds_model *model, const int32_t *origins, int64_t norigin, const double *hkl,
                                    int64_t npts, int hkl_is_device, const ds_opts *opts, void *out, int out_is_device,
                                    void *stream, ds_result_info *info);
