@@ -761,6 +761,46 @@ def test_perovskite_64cubed_displacive_full_size():
     assert np.all(np.abs(got - want) <= 1e-5 * float(sm.max()) + 1e-4 * np.abs(want))
 
 
+def test_subbox_random_displacive_fcc32_plane_full_size():
+    """The sub-box row at full size: fcc 32^3, u ~ N(0, 0.1^2), n_sb = 5, random origins covering
+    every lattice point, (h h l) plane 201 x 201 on the device, DIFFUSE, FP32: sampled points
+    (one on a Bragg position) against the oracle's loop over the same origins; the FP64 path on
+    the same points within 1e-10."""
+    import torch
+    m = syn.displacive_fcc(cells=(32, 32, 32), sigma=0.1, seed=5)
+    lm = to_library(ctx_holder(), m)
+    org = syn.covering_origins(np.random.default_rng(7), 1, m.cells, 5)
+    u, v = np.meshgrid(np.linspace(-5.0, 5.0, 201), np.linspace(-5.0, 5.0, 201), indexing="ij")
+    hkl = np.stack([u.ravel(), u.ravel(), v.ravel()], axis=1)
+    out = torch.empty(hkl.shape[0], dtype=torch.float32, device="cuda")
+    lm.subbox_points(torch.from_numpy(hkl).cuda(), org, out=out, disorder=2, mode=1, precision=1, subbox_n=5)
+    torch.cuda.synchronize()
+    pick = np.concatenate([np.random.default_rng(11).choice(hkl.shape[0], 7, replace=False), [100 * 201 + 100]])
+    want = noise.subbox_intensity(m, "disp", 1, 5, hkl[pick], org)
+    peak = float(out.max())
+    assert np.max(np.abs(out.cpu().numpy()[pick] - want)) < 1e-5 * peak
+    g64, _ = lm.subbox_points(hkl[pick], org, disorder=2, mode=1, precision=0, subbox_n=5)
+    assert rel_err_of_peak(g64, want) < TOL["fp64"]
+
+
+def test_magnetic_debye_waller_pyrochlore20_full_size():
+    """The Debye-Waller coupling row at full size: magnetic pyrochlore 20^3 with u ~ N(0, 0.05^2),
+    |h,k,l| <= 2 step 1/20 (81^3 voxels), FP32 on the device: sampled voxels (Q = 0 included)
+    against the oracle's direct sum with T_mu(G)."""
+    import torch
+    m = syn.pyrochlore_mag_disp(cells=(20, 20, 20), hmax=2.0)
+    lm = to_library(ctx_holder(), m)
+    out = torch.empty(m.qgrid.count, dtype=torch.float32, device="cuda")
+    lm.intensity(qgrid_tuple(m.qgrid), out=out, disorder=1, mode=0, precision=1, dw_coupling=1)
+    torch.cuda.synchronize()
+    idx = np.concatenate([np.random.default_rng(12).choice(m.qgrid.nvox, 300, replace=False),
+                          [np.ravel_multi_index((40, 40, 40), m.qgrid.count)]])
+    hkl = sample_G(m, idx) / 20.0
+    want = core.magnetic_intensity_direct(m, hkl, 0, dw=True)
+    got = out.reshape(-1)[torch.from_numpy(idx).cuda()].double().cpu().numpy()
+    assert np.max(np.abs(got - want)) < 1e-5 * float(out.max())
+
+
 _CTX = []
 
 
