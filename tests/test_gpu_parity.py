@@ -378,13 +378,14 @@ def test_grouped_sites_several_form_factor_classes(ctx, dis):
         assert rel_err_of_peak(got, want) < TOL[tag]
 
 
-def _special_positions_case(kind, nsite, ff, seed):
+def _special_positions_case(kind, nsite, ff, seed, cells=(5, 6, 4), shift=0):
     """Sites on multiples of 1/4, 1/3 and 1/2 along the three axes (zone phases periodic in H
-    with periods 4, 3, 2; suffix _xr: random first coordinates), a triclinic cell, two supercells and a ragged grid of 6 zones per
-    axis, so that the residue-class recombination applies."""
-    cells = (5, 6, 4)
-    q = syn.QGrid(h0=tuple(-3.0 + 3.0 / n for n in cells), step=tuple(1.0 / n for n in cells),
-                  count=tuple(6 * n - 5 for n in cells))
+    with periods 4, 3, 2; suffix _xr: random first coordinates), a triclinic cell, two
+    supercells and a ragged grid of 6 zones per axis, so that the residue-class recombination
+    applies.  The grid is centrosymmetric (the half-grid Friedel mode) unless `shift` moves it by
+    that many voxels along the last axis."""
+    q = syn.QGrid(h0=tuple(-3.0 + 3.0 / n for n in cells[:2]) + (-3.0 + (3.0 + shift) / cells[2],),
+                  step=tuple(1.0 / n for n in cells), count=tuple(6 * n - 5 for n in cells))
     m = syn.small_case(kind, cells=cells, nsite=nsite, nmodels=2, seed=seed, qgrid=q)
     rng = np.random.default_rng(seed)
     m.sites = np.stack([rng.integers(0, 4, nsite) / 4.0, rng.integers(0, 3, nsite) / 3.0,
@@ -415,6 +416,23 @@ def test_residue_classes_special_positions(ctx, prec, tag, disorder, nsite, ff, 
     got, _ = lm.intensity(qgrid_tuple(m.qgrid), disorder=disorder, mode=mode, precision=prec)
     fn = core.occupancy_intensity_fft if disorder == 0 else core.magnetic_intensity_fft
     assert rel_err_of_peak(got, fn(m, G, mode)) < TOL[tag]
+
+
+@pytest.mark.parametrize("prec,tag", PREC)
+@pytest.mark.parametrize("cells,shift", [((5, 6, 4), 0), ((4, 6, 5), 0), ((5, 4, 7), 0), ((5, 6, 4), 1),
+                                         ((4, 6, 5), -2)])
+@pytest.mark.parametrize("disorder,ff", [(0, "one_j0"), (1, "one_j0"), (1, "mixed")])
+def test_residue_classes_centred_and_shifted_grids(ctx, prec, tag, cells, shift, disorder, ff):
+    """Residue-class recombination on centrosymmetric grids with even and odd n3 and on shifted
+    grids, two supercells accumulated: voxel by voxel equal to the oracle, and I(-G) = I(G)
+    (Friedel symmetry of real fields) within the tolerance when the grid is centred."""
+    m = _special_positions_case(disorder, 6, ff, 400 + disorder, cells=cells, shift=shift)
+    lm = to_library(ctx, m)
+    got, _ = lm.intensity(qgrid_tuple(m.qgrid), disorder=disorder, mode=1 - disorder, precision=prec)
+    fn = core.occupancy_intensity_fft if disorder == 0 else core.magnetic_intensity_fft
+    assert rel_err_of_peak(got, fn(m, _G(m), 1 - disorder)) < TOL[tag]
+    if shift == 0:
+        assert rel_err_of_peak(got, got[::-1, ::-1, ::-1]) < TOL[tag]
 
 
 @pytest.mark.parametrize("disorder,kind", [("occ", 0), ("spin", 1)])
