@@ -88,6 +88,12 @@ static bool plan_axis(int n, AxisPlan &p) {
             m /= r;
         }
     }
+    int Ns = 1;
+    for (int q = 0; q < p.nrad; ++q) {
+        p.mNR[q] = FastDiv::magic((unsigned)(n / p.rad[q]));
+        p.mNs[q] = FastDiv::magic((unsigned)Ns);
+        Ns *= p.rad[q];
+    }
     return m == 1;
 }
 

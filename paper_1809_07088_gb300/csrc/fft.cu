@@ -88,9 +88,10 @@ __global__ void k_fft_planes(Geometry g, FieldSource src, int f0, int ppc, c_t<T
 
     // load: complex line p of plane q holds rows 2p (real) and 2p + 1 (imaginary)
     const int per_plane_in = n2p * n3;
+    const FastDiv fin((unsigned)per_plane_in), f3((unsigned)n3), fh((unsigned)n3h), fph((unsigned)(n2 * n3h));
     for (int idx = threadIdx.x; idx < np * per_plane_in; idx += blockDim.x) {
-        const int q = idx / per_plane_in, rem = idx - q * per_plane_in;
-        const int p = rem / n3, r3 = rem - p * n3;
+        const int q = (int)fin.div((unsigned)idx), rem = idx - q * per_plane_in;
+        const int p = (int)f3.div((unsigned)rem), r3 = rem - p * n3;
         const int cell0 = ((r1_0 + q) * n2 + 2 * p) * n3 + r3;
         const T x = source_value<T>(src, ncell, f, cell0);
         const T y = (2 * p + 1 < n2) ? source_value<T>(src, ncell, f, cell0 + n3) : T(0);
@@ -103,11 +104,11 @@ __global__ void k_fft_planes(Geometry g, FieldSource src, int f0, int ppc, c_t<T
     // separate the packed rows: X = (Z + conj Z-)/2, Y = (Z - conj Z-)/(2i), keep k3 < n3h
     const int per_plane_h = n2 * n3h;
     for (int idx = threadIdx.x; idx < np * per_plane_h; idx += blockDim.x) {
-        const int q = idx / per_plane_h, rem = idx - q * per_plane_h;
-        const int row = rem / n3h, k3 = rem - row * n3h;
+        const int q = (int)fph.div((unsigned)idx), rem = idx - q * per_plane_h;
+        const int row = (int)fh.div((unsigned)rem), k3 = rem - row * n3h;
         const int p = row >> 1;
         const C z = res[(size_t)q * plane_c + p * n3 + k3];
-        const C zm = res[(size_t)q * plane_c + p * n3 + (n3 - k3) % n3];
+        const C zm = res[(size_t)q * plane_c + p * n3 + (k3 == 0 ? 0 : n3 - k3)];
         C v;
         if ((row & 1) == 0)
             v = mk<T>(T(0.5) * (z.x + zm.x), T(0.5) * (z.y - zm.y));
@@ -120,7 +121,7 @@ __global__ void k_fft_planes(Geometry g, FieldSource src, int f0, int ppc, c_t<T
     C *res2 = fft_lines<T>(dst, res, g.ax[1], W2, np * n3h, n3h, 1, plane_c, n3h);
     C *out = work + ((size_t)fl * n1 + r1_0) * per_plane_h;
     for (int idx = threadIdx.x; idx < np * per_plane_h; idx += blockDim.x) {
-        const int q = idx / per_plane_h, rem = idx - q * per_plane_h;
+        const int q = (int)fph.div((unsigned)idx), rem = idx - q * per_plane_h;
         out[(size_t)q * per_plane_h + rem] = res2[(size_t)q * plane_c + rem];
     }
 }
@@ -141,8 +142,9 @@ __global__ void k_fft_columns(Geometry g, FieldSource src, int f0, int cb, const
     const int f = f0 + fl;
     const int c0 = (blockIdx.x - fl * nchunk) * cb;
     const C *in = work + (size_t)fl * n1 * ncol;
+    const FastDiv fcb((unsigned)cb);
     for (int idx = threadIdx.x; idx < n1 * cb; idx += blockDim.x) {
-        const int r1 = idx / cb, c = idx - r1 * cb;
+        const int r1 = (int)fcb.div((unsigned)idx), c = idx - r1 * cb;
         bufA[idx] = (c0 + c < ncol) ? in[(size_t)r1 * ncol + c0 + c] : mk<T>(T(0), T(0));
     }
     __syncthreads();
@@ -154,7 +156,7 @@ __global__ void k_fft_columns(Geometry g, FieldSource src, int f0, int cb, const
     }
     C *out = spec + (size_t)f * g.ncell_h;
     for (int idx = threadIdx.x; idx < n1 * cb; idx += blockDim.x) {
-        const int k1 = idx / cb, c = idx - k1 * cb;
+        const int k1 = (int)fcb.div((unsigned)idx), c = idx - k1 * cb;
         if (c0 + c < ncol) out[(size_t)k1 * ncol + c0 + c] = cipow(res[idx], rot);
     }
 }
@@ -182,9 +184,11 @@ __global__ void __launch_bounds__(512) k_fft_field(Geometry g, FieldSource src, 
     const int f = f0 + blockIdx.x;
     const int ncell = g.ncell;
     const int per_plane_in = n2p * n3;
+    const int per_plane_h = n2 * n3h;
+    const FastDiv fin((unsigned)per_plane_in), f3((unsigned)n3), fh((unsigned)n3h), fph((unsigned)per_plane_h);
     for (int idx = threadIdx.x; idx < n1 * per_plane_in; idx += blockDim.x) {
-        const int q = idx / per_plane_in, rem = idx - q * per_plane_in;
-        const int pr = rem / n3, r3 = rem - pr * n3;
+        const int q = (int)fin.div((unsigned)idx), rem = idx - q * per_plane_in;
+        const int pr = (int)f3.div((unsigned)rem), r3 = rem - pr * n3;
         const int cell0 = (q * n2 + 2 * pr) * n3 + r3;
         const T x = source_value<T>(src, ncell, f, cell0);
         const T y = (2 * pr + 1 < n2) ? source_value<T>(src, ncell, f, cell0 + n3) : T(0);
@@ -193,13 +197,12 @@ __global__ void __launch_bounds__(512) k_fft_field(Geometry g, FieldSource src, 
     __syncthreads();
     C *res = fft_lines<T>(bufA, bufB, g.ax[2], W3, n1 * n2p, n2p, n3, plane_c, 1);
     C *dst = (res == bufA) ? bufB : bufA;
-    const int per_plane_h = n2 * n3h;
     for (int idx = threadIdx.x; idx < n1 * per_plane_h; idx += blockDim.x) {
-        const int q = idx / per_plane_h, rem = idx - q * per_plane_h;
-        const int row = rem / n3h, k3 = rem - row * n3h;
+        const int q = (int)fph.div((unsigned)idx), rem = idx - q * per_plane_h;
+        const int row = (int)fh.div((unsigned)rem), k3 = rem - row * n3h;
         const int pr = row >> 1;
         const C z = res[(size_t)q * plane_c + pr * n3 + k3];
-        const C zm = res[(size_t)q * plane_c + pr * n3 + (n3 - k3) % n3];
+        const C zm = res[(size_t)q * plane_c + pr * n3 + (k3 == 0 ? 0 : n3 - k3)];
         C v;
         if ((row & 1) == 0)
             v = mk<T>(T(0.5) * (z.x + zm.x), T(0.5) * (z.y - zm.y));
@@ -219,7 +222,7 @@ __global__ void __launch_bounds__(512) k_fft_field(Geometry g, FieldSource src, 
     }
     C *out = spec + (size_t)f * g.ncell_h;
     for (int idx = threadIdx.x; idx < n1 * per_plane_h; idx += blockDim.x) {
-        const int k1 = idx / per_plane_h, rem = idx - k1 * per_plane_h;
+        const int k1 = (int)fph.div((unsigned)idx), rem = idx - k1 * per_plane_h;
         out[idx] = cipow(res3[(size_t)k1 * plane_c + rem], rot);
     }
 }

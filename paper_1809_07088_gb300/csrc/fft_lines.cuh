@@ -14,10 +14,24 @@
 
 namespace ds {
 
+// Exact x / d for x d < 2^32 by a high multiply: m = ceil(2^32 / d) (0 stands for d = 1); with
+// x = q d + r, x m / 2^32 = q + (r + x e / 2^32) / d, e = m d - 2^32 < d, and x e < x d < 2^32
+// keeps the fraction below 1.  The FFT index arithmetic (counts below 2^24 whose products with
+// their divisors stay below 2^32 for supercells of up to 128 cells per axis) uses it instead of
+// integer division; the per-pass divisors come with the axis plan, built on the host.
+struct FastDiv {
+    unsigned d, m;
+    __host__ __device__ __forceinline__ static unsigned magic(unsigned dd) { return dd == 1 ? 0u : 0xFFFFFFFFu / dd + 1u; }
+    __host__ __device__ __forceinline__ FastDiv(unsigned dd, unsigned mm) : d(dd), m(mm) {}
+    __host__ __device__ __forceinline__ explicit FastDiv(unsigned dd) : d(dd), m(magic(dd)) {}
+    __device__ __forceinline__ unsigned div(unsigned x) const { return m ? __umulhi(x, m) : x; }
+};
+
 struct AxisPlan {
     int n;       // transform length
     int nrad;    // number of radix passes
     int rad[8];  // radices in pass order
+    unsigned mNR[8], mNs[8];  // FastDiv magics of n / rad[p] and of the running product Ns before pass p
 };
 
 constexpr int MAX_RADIX = 7;
@@ -97,33 +111,37 @@ __device__ c_t<T> *fft_lines(c_t<T> *a, c_t<T> *b, const AxisPlan &P, const c_t<
     const int n = P.n;
     int Ns = 1;
     const bool j_fast = (estride == 1);
+    const FastDiv finner((unsigned)inner), flines((unsigned)nlines);
     for (int p = 0; p < P.nrad; ++p) {
         const int R = P.rad[p];
         const int NR = n / R;
         const int tw = n / (Ns * R);
         const int tasks = nlines * NR;
+        const FastDiv fNR((unsigned)NR, P.mNR[p]), fNs((unsigned)Ns, P.mNs[p]);
         for (int task = threadIdx.x; task < tasks; task += blockDim.x) {
             int L, j;
             if (j_fast) {
-                j = task % NR;
-                L = task / NR;
+                L = (int)fNR.div((unsigned)task);
+                j = task - L * NR;
             } else {
-                L = task % nlines;
-                j = task / nlines;
+                j = (int)flines.div((unsigned)task);
+                L = task - j * nlines;
             }
-            const int base = (L / inner) * outer_stride + (L % inner) * inner_stride;
-            const int k = j % Ns;
+            const int Lo = (int)finner.div((unsigned)L);
+            const int base = Lo * outer_stride + (L - Lo * inner) * inner_stride;
+            const int k = j - (int)fNs.div((unsigned)j) * Ns;
             C v[MAX_RADIX];
 #pragma unroll
             for (int r = 0; r < MAX_RADIX; ++r) {
                 if (r < R) {
                     C x = a[base + (j + r * NR) * estride];
-                    if (r > 0) x = cmul(x, W[(k * r * tw) % n]);
+                    // k r tw < Ns R tw = n: the root index needs no reduction
+                    if (r > 0) x = cmul(x, W[k * r * tw]);
                     v[r] = x;
                 }
             }
             dft_small<C, T>(v, R);
-            const int idxD = (j / Ns) * Ns * R + k;
+            const int idxD = (j - k) * R + k;  // (j / Ns) Ns R + k
 #pragma unroll
             for (int r = 0; r < MAX_RADIX; ++r)
                 if (r < R) b[base + (idxD + r * Ns) * estride] = v[r];
