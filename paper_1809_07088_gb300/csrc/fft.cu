@@ -30,37 +30,69 @@ template <typename T> void make_twiddles(int n, c_t<T> *W, cudaStream_t s) {
     count_launches(1);
 }
 
-// value of real field f at lattice point `cell` (linear [R1][R2][R3])
-template <typename T>
-__device__ __forceinline__ T source_value(const FieldSource &src, int ncell, int f, int cell) {
+// The rows of model data that make up real field f, resolved once per CTA so that the per-cell
+// value is a few loads and multiplies (no division by the field counts in the load loops).
+template <typename T> struct FieldRow {
+    int kind;
+    const uint8_t *occ;  // occupancy row (SRC_OCC; SRC_DISP weights, may be null)
+    const float *vec;    // moment row, component `comp` (SRC_SPIN)
+    const T *pw[3];      // power rows (u_a Q_s)^e_a / e_a! (SRC_DISP)
+    const T *real;       // SRC_REAL row
+    int comp;
+    T mean;              // subtracted site mean (SRC_OCC / SRC_SPIN, DIFFUSE), else 0
+};
+
+template <typename T> __device__ __forceinline__ FieldRow<T> field_row(const FieldSource &src, int ncell, int f) {
+    FieldRow<T> r;
+    r.kind = src.kind;
+    r.occ = nullptr;
+    r.vec = nullptr;
+    r.pw[0] = r.pw[1] = r.pw[2] = nullptr;
+    r.real = nullptr;
+    r.comp = 0;
+    r.mean = T(0);
     const int m = f / src.nf_per_model;
     const int lf = f - m * src.nf_per_model;
     switch (src.kind) {
-    case SRC_OCC: {
-        const int mu = lf;
-        T v = (T)src.occ[((size_t)m * src.nsite + mu) * ncell + cell];
-        if (src.diffuse) v -= (T)src.mean[mu];
-        return v;
-    }
+    case SRC_OCC:
+        r.occ = src.occ + ((size_t)m * src.nsite + lf) * ncell;
+        if (src.diffuse) r.mean = (T)src.mean[lf];
+        break;
     case SRC_SPIN: {
         const int mu = lf / 3, a = lf - 3 * mu;
-        T v = (T)src.vec3[(((size_t)m * src.nsite + mu) * ncell + cell) * 3 + a];
-        if (src.diffuse) v -= (T)src.mean[mu * 3 + a];
-        return v;
+        r.vec = src.vec3 + ((size_t)m * src.nsite + mu) * ncell * 3;
+        r.comp = a;
+        if (src.diffuse) r.mean = (T)src.mean[mu * 3 + a];
+        break;
     }
     case SRC_DISP: {
         const int mu = lf / src.T, t = lf - mu * src.T;
         const int4 e = src.terms[t];
-        const T *pw = (const T *)src.pw;
         const size_t P1 = (size_t)src.P + 1;
-        const size_t base = (((size_t)m * src.nsite + mu) * 3) * P1 * ncell;
-        T v = pw[base + (0 * P1 + e.x) * ncell + cell] * pw[base + (1 * P1 + e.y) * ncell + cell] *
-              pw[base + (2 * P1 + e.z) * ncell + cell];
-        if (src.occ) v *= (T)src.occ[((size_t)m * src.nsite + mu) * ncell + cell];
-        return v;
+        const T *base = (const T *)src.pw + (((size_t)m * src.nsite + mu) * 3) * P1 * ncell;
+        r.pw[0] = base + (0 * P1 + e.x) * ncell;
+        r.pw[1] = base + (1 * P1 + e.y) * ncell;
+        r.pw[2] = base + (2 * P1 + e.z) * ncell;
+        if (src.occ) r.occ = src.occ + ((size_t)m * src.nsite + mu) * ncell;
+        break;
     }
     default:
-        return ((const T *)src.real_buf)[(size_t)f * ncell + cell];
+        r.real = (const T *)src.real_buf + (size_t)f * ncell;
+    }
+    return r;
+}
+
+// value of the field at lattice point `cell` (linear [R1][R2][R3])
+template <typename T> __device__ __forceinline__ T row_value(const FieldRow<T> &r, int cell) {
+    switch (r.kind) {
+    case SRC_OCC: return (T)r.occ[cell] - r.mean;
+    case SRC_SPIN: return (T)r.vec[(size_t)cell * 3 + r.comp] - r.mean;
+    case SRC_DISP: {
+        T v = r.pw[0][cell] * r.pw[1][cell] * r.pw[2][cell];
+        if (r.occ) v *= (T)r.occ[cell];
+        return v;
+    }
+    default: return r.real[cell];
     }
 }
 
@@ -85,6 +117,7 @@ __global__ void k_fft_planes(Geometry g, FieldSource src, int f0, int ppc, c_t<T
     const int r1_0 = (blockIdx.x - fl * nchunk) * ppc;
     const int np = min(ppc, n1 - r1_0);
     const int ncell = g.ncell;
+    const FieldRow<T> fr = field_row<T>(src, ncell, f);
 
     // load: complex line p of plane q holds rows 2p (real) and 2p + 1 (imaginary)
     const int per_plane_in = n2p * n3;
@@ -93,8 +126,8 @@ __global__ void k_fft_planes(Geometry g, FieldSource src, int f0, int ppc, c_t<T
         const int q = (int)fin.div((unsigned)idx), rem = idx - q * per_plane_in;
         const int p = (int)f3.div((unsigned)rem), r3 = rem - p * n3;
         const int cell0 = ((r1_0 + q) * n2 + 2 * p) * n3 + r3;
-        const T x = source_value<T>(src, ncell, f, cell0);
-        const T y = (2 * p + 1 < n2) ? source_value<T>(src, ncell, f, cell0 + n3) : T(0);
+        const T x = row_value<T>(fr, cell0);
+        const T y = (2 * p + 1 < n2) ? row_value<T>(fr, cell0 + n3) : T(0);
         bufA[(size_t)q * plane_c + p * n3 + r3] = mk<T>(x, y);
     }
     __syncthreads();
@@ -183,6 +216,7 @@ __global__ void __launch_bounds__(512) k_fft_field(Geometry g, FieldSource src, 
     for (int i = threadIdx.x; i < n3; i += blockDim.x) W3[i] = W3g[i];
     const int f = f0 + blockIdx.x;
     const int ncell = g.ncell;
+    const FieldRow<T> fr = field_row<T>(src, ncell, f);
     const int per_plane_in = n2p * n3;
     const int per_plane_h = n2 * n3h;
     const FastDiv fin((unsigned)per_plane_in), f3((unsigned)n3), fh((unsigned)n3h), fph((unsigned)per_plane_h);
@@ -190,8 +224,8 @@ __global__ void __launch_bounds__(512) k_fft_field(Geometry g, FieldSource src, 
         const int q = (int)fin.div((unsigned)idx), rem = idx - q * per_plane_in;
         const int pr = (int)f3.div((unsigned)rem), r3 = rem - pr * n3;
         const int cell0 = (q * n2 + 2 * pr) * n3 + r3;
-        const T x = source_value<T>(src, ncell, f, cell0);
-        const T y = (2 * pr + 1 < n2) ? source_value<T>(src, ncell, f, cell0 + n3) : T(0);
+        const T x = row_value<T>(fr, cell0);
+        const T y = (2 * pr + 1 < n2) ? row_value<T>(fr, cell0 + n3) : T(0);
         bufA[(size_t)q * plane_c + pr * n3 + r3] = mk<T>(x, y);
     }
     __syncthreads();

@@ -34,7 +34,6 @@ struct AxisPlan {
     unsigned mNR[8], mNs[8];  // FastDiv magics of n / rad[p] and of the running product Ns before pass p
 };
 
-constexpr int MAX_RADIX = 7;
 
 template <typename C, typename T> __device__ __forceinline__ void dft_small(C *v, int R) {
     // r-point DFT with the +i sign, in place
@@ -100,6 +99,42 @@ template <typename C, typename T> __device__ __forceinline__ void dft_small(C *v
     }
 }
 
+// One Stockham pass of compile-time radix R over every line of the batch (see fft_lines).
+template <typename T, int R>
+__device__ __forceinline__ void radix_pass(const c_t<T> *__restrict__ a, c_t<T> *__restrict__ b, const c_t<T> *W,
+                                           int NR, int Ns, int tw, int nlines, int inner_stride, int outer_stride,
+                                           int estride, bool j_fast, const FastDiv &fNR, const FastDiv &fNs,
+                                           const FastDiv &flines, const FastDiv &finner) {
+    using C = c_t<T>;
+    const int tasks = nlines * NR;
+    const int inner = (int)finner.d;
+    for (int task = threadIdx.x; task < tasks; task += blockDim.x) {
+        int L, j;
+        if (j_fast) {
+            L = (int)fNR.div((unsigned)task);
+            j = task - L * NR;
+        } else {
+            j = (int)flines.div((unsigned)task);
+            L = task - j * nlines;
+        }
+        const int Lo = (int)finner.div((unsigned)L);
+        const int base = Lo * outer_stride + (L - Lo * inner) * inner_stride;
+        const int k = j - (int)fNs.div((unsigned)j) * Ns;
+        C v[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            C x = a[base + (j + r * NR) * estride];
+            // k r tw < Ns R tw = n: the root index needs no reduction
+            if (r > 0) x = cmul(x, W[k * r * tw]);
+            v[r] = x;
+        }
+        dft_small<C, T>(v, R);
+        const int idxD = (j - k) * R + k;  // (j / Ns) Ns R + k
+#pragma unroll
+        for (int r = 0; r < R; ++r) b[base + (idxD + r * Ns) * estride] = v[r];
+    }
+}
+
 // Transform nlines lines of length P.n.  Element e of line L lives at
 //     (L / inner) * outer_stride + (L % inner) * inner_stride + e * estride
 // in buffer `a`; `b` is a same-sized scratch buffer.  Returns the buffer that holds the result.
@@ -116,35 +151,13 @@ __device__ c_t<T> *fft_lines(c_t<T> *a, c_t<T> *b, const AxisPlan &P, const c_t<
         const int R = P.rad[p];
         const int NR = n / R;
         const int tw = n / (Ns * R);
-        const int tasks = nlines * NR;
         const FastDiv fNR((unsigned)NR, P.mNR[p]), fNs((unsigned)Ns, P.mNs[p]);
-        for (int task = threadIdx.x; task < tasks; task += blockDim.x) {
-            int L, j;
-            if (j_fast) {
-                L = (int)fNR.div((unsigned)task);
-                j = task - L * NR;
-            } else {
-                j = (int)flines.div((unsigned)task);
-                L = task - j * nlines;
-            }
-            const int Lo = (int)finner.div((unsigned)L);
-            const int base = Lo * outer_stride + (L - Lo * inner) * inner_stride;
-            const int k = j - (int)fNs.div((unsigned)j) * Ns;
-            C v[MAX_RADIX];
-#pragma unroll
-            for (int r = 0; r < MAX_RADIX; ++r) {
-                if (r < R) {
-                    C x = a[base + (j + r * NR) * estride];
-                    // k r tw < Ns R tw = n: the root index needs no reduction
-                    if (r > 0) x = cmul(x, W[k * r * tw]);
-                    v[r] = x;
-                }
-            }
-            dft_small<C, T>(v, R);
-            const int idxD = (j - k) * R + k;  // (j / Ns) Ns R + k
-#pragma unroll
-            for (int r = 0; r < MAX_RADIX; ++r)
-                if (r < R) b[base + (idxD + r * Ns) * estride] = v[r];
+        switch (R) {
+        case 4: radix_pass<T, 4>(a, b, W, NR, Ns, tw, nlines, inner_stride, outer_stride, estride, j_fast, fNR, fNs, flines, finner); break;
+        case 2: radix_pass<T, 2>(a, b, W, NR, Ns, tw, nlines, inner_stride, outer_stride, estride, j_fast, fNR, fNs, flines, finner); break;
+        case 3: radix_pass<T, 3>(a, b, W, NR, Ns, tw, nlines, inner_stride, outer_stride, estride, j_fast, fNR, fNs, flines, finner); break;
+        case 5: radix_pass<T, 5>(a, b, W, NR, Ns, tw, nlines, inner_stride, outer_stride, estride, j_fast, fNR, fNs, flines, finner); break;
+        default: radix_pass<T, 7>(a, b, W, NR, Ns, tw, nlines, inner_stride, outer_stride, estride, j_fast, fNR, fNs, flines, finner); break;
         }
         __syncthreads();
         C *t = a;
