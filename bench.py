@@ -437,6 +437,33 @@ def run_ours(args):
 # the other rows of the path, each timed on its own workload (device events, warm)
 # ----------------------------------------------------------------------------------------------
 
+def fft_side_comparison(dev, nfields, cells, ours_ms, reps=3):
+    """Timed side comparison, not on the path: cuFFT (through torch.fft.rfftn) on the same batch
+    of real fields, materialised in HBM (the library generates the monomials inside its first
+    pass instead).  Returns a dict, or the reason it could not run."""
+    import torch
+    try:
+        x = torch.randn((nfields,) + tuple(cells), dtype=torch.float32, device=dev)
+        torch.fft.rfftn(x, dim=(-3, -2, -1))
+        torch.cuda.synchronize(dev)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(reps):
+            y = torch.fft.rfftn(x, dim=(-3, -2, -1))
+        b.record()
+        torch.cuda.synchronize(dev)
+        ms = a.elapsed_time(b) / reps
+        nbytes = x.numel() * 4 + y.numel() * 8
+        del x, y
+        torch.cuda.empty_cache()
+        return {"library": "cuFFT via torch.fft.rfftn (forward, R2C, FP32)", "fields": nfields,
+                "cells": list(cells), "ms": ms, "library_GBps": nbytes / (ms / 1e3) / 1e9,
+                "ours_ms": ours_ms,
+                "note": "side comparison only; the library's FFT stage also generates the monomial fields"}
+    except Exception as e:  # the comparison must never stop the bench
+        return {"unavailable": "%s: %s" % (type(e).__name__, str(e)[:200])}
+
+
 def run_rows(dev):
     """One measurement per remaining step of the path: the Taylor (displacive) recombination and
     its adjoint on the fcc 32^3 / 321^3 case, Lanczos resampling on a 1025^3 volume, exact sub-box
@@ -498,6 +525,10 @@ def run_rows(dev):
     ms, st = timed(lambda: lm.backward(q, dL, grad=g, disorder=ds.DS_DISP, mode=ds.DS_TOTAL, precision=ds.DS_FP32,
                                        taylor_order=-1, taylor_eps=1e-8), reps=2)
     rows["adjoint_fcc32"] = {"workload": "dchi2/du of the fcc 32^3 case above, FP32", "ms": ms, "stages_ms": st}
+    # side comparison only (not on the path): the library FFT of the same batch of fields
+    nf_fcc = m.nsite * rows["taylor_fcc32_zonal0"]["monomials"]
+    rows["fft_side_comparison"] = fft_side_comparison(dev, nf_fcc, m.cells,
+                                                      rows["taylor_fcc32_zonal0"]["stages_ms"].get("fft"))
     lm.close()
     del out, dL, g
 
