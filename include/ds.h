@@ -246,10 +246,13 @@ ds_status ds_profile_report(ds_ctx *ctx, char *json, size_t cap);
  *   grid, mode      as for ds_request_intensity (commensurate grid; DS_TOTAL / DS_DIFFUSE)
  *   out_dev         device float [count0][count1][count2], written in stream order on `stream`
  *   err, errlen     optional buffer for a message on failure
- * Requests whose scratch exceeds 32 MiB return DS_ERR_ADMISSION (message gives the size).
- * The first call on a device looks up the array's address with that device current: make it
- * before any stream capture.  All calls share the array; calls whose GPU work overlaps race on
- * it and must be serialised by the caller.  Nothing in the array needs clearing between calls. */
+ * Requests whose scratch exceeds 32 MiB return DS_ERR_ADMISSION (message gives the size); a
+ * non-finite site coordinate, scattering length or mean returns DS_ERR_ARG.  The per-site inputs
+ * are passed to the GPU by value: no host buffer is read after the call returns.
+ * The first call on a device (and the first after that device's context was reset) looks up the
+ * array's address with that device current: make that call before any stream capture on the
+ * device.  All calls share the array; calls whose GPU work overlaps race on it and must be
+ * serialised by the caller.  Nothing in the array needs clearing between calls. */
 ds_status ds_occupancy_intensity_noalloc(const double lattice[6], int nsite, const double *frac_xyz,
                                          const double *scat_len, int n1, int n2, int n3, int nmodels,
                                          const uint8_t *occ_dev, const double *mean_occ, const ds_qgrid *grid,

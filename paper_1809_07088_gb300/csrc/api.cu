@@ -461,6 +461,8 @@ extern "C" ds_status ds_model_set_sites(ds_model *m, int nsite, const double *xy
 // list, with their coefficient update codes: [map | ops | off[P+2]] on the device, per model
 static ds_status sub_simplex_tables(ds_model *m, int P, int **tab) {
     ds_ctx *ctx = m->ctx;
+    // the serving worker and caller threads plan requests on the same model concurrently
+    std::lock_guard<std::mutex> lk(m->cache_mu);
     auto it = m->sub_tables.find(P);
     if (it != m->sub_tables.end()) {
         *tab = it->second;
@@ -504,6 +506,7 @@ static ds_status taylor_tables(ds_model *m, int P, int4 **terms, int **ops, int 
     std::vector<int> o;
     monomial_tables(P, t, o);
     *T = (int)t.size();
+    std::lock_guard<std::mutex> lk(m->cache_mu);
     auto it = m->taylor_tables.find(P);
     if (it == m->taylor_tables.end()) {
         int4 *dt = nullptr;

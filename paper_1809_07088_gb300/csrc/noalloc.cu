@@ -6,14 +6,17 @@
 // a refinement loop that must not touch the allocator between iterations.  This entry point
 // serves them: it computes the same result as ds_request_intensity for occupancy disorder with
 // constant form factors in FP32, but every intermediate (twiddles, site-phase tables, site
-// means, per-site spectra, FFT work buffer) lives in one file-scope device array of fixed size,
-// g_noalloc_scratch.  The caller passes the inputs and the output; nothing is allocated.
+// data and means, per-site spectra, FFT work buffer) lives in one file-scope device array of
+// fixed size, g_noalloc_scratch.  The caller passes the inputs and the output; nothing is
+// allocated.  The per-site inputs (at most 32 sites) travel as a kernel argument, so no host
+// buffer is read after the call returns.
 //
 // Properties a caller must know:
 //  - The array is DS_NOALLOC_SCRATCH_BYTES (32 MiB) on every GPU that loads the library and stays
 //    there until the process exits.  Requests needing more are rejected with DS_ERR_ADMISSION.
-//  - The first call on a device looks up the array's device address (cudaGetSymbolAddress) with
-//    that device current; make that first call before any stream capture on the device.
+//  - The first call on a device (and the first after that device's context was reset) looks up
+//    the array's device address (cudaGetSymbolAddress) with that device current; make that call
+//    before any stream capture on the device.
 //  - All calls share the array.  Every kernel writes the scratch it reads before reading it, so
 //    no part of the array has to start at zero, but two calls whose work overlaps on the GPU
 //    (different streams, or several host threads) race on it: serialise them.
@@ -38,8 +41,18 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[DS_NOALLOC_SCRA
 namespace {
 
 constexpr int kMaxDevices = 64;
+constexpr int kMaxSites = 32;
+
+// per-device cache of the array's address, valid for the context it was looked up in
+struct ScratchAddr {
+    unsigned long long ctx_id = 0;
+    bool have_id = false;
+    unsigned char *addr = nullptr;
+};
 std::mutex g_addr_mu;
-unsigned char *g_addr[kMaxDevices] = {nullptr};
+ScratchAddr g_addr[kMaxDevices];
+
+typedef int (*ctx_get_id_fn)(void *ctx, unsigned long long *id);  // cuCtxGetId(NULL = current)
 
 ds_status say(char *err, size_t errlen, ds_status st, const char *fmt, ...) {
     if (err && errlen) {
@@ -51,19 +64,60 @@ ds_status say(char *err, size_t errlen, ds_status st, const char *fmt, ...) {
     return st;
 }
 
-// device address of the static scratch on the current device (looked up once per device)
+// unique id of the current context (false when the driver cannot tell)
+bool current_context_id(unsigned long long *id) {
+    static ctx_get_id_fn fn = nullptr;
+    static bool looked = false;
+    if (!looked) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (ctx_get_id_fn)p;
+        cudaGetLastError();
+        looked = true;
+    }
+    return fn && fn(nullptr, id) == 0;
+}
+
+// device address of the static scratch on device `dev` (current): looked up once per device
+// context, again when the context changed (a reset unloads the module and the array may move)
 ds_status scratch_address(int dev, unsigned char **out, char *err, size_t errlen) {
     if (dev < 0 || dev >= kMaxDevices) return say(err, errlen, DS_ERR_ARG, "device %d out of range", dev);
     std::lock_guard<std::mutex> g(g_addr_mu);
-    if (!g_addr[dev]) {
+    ScratchAddr &c = g_addr[dev];
+    unsigned long long id = 0;
+    const bool have_id = current_context_id(&id);
+    if (!c.addr || !have_id || !c.have_id || c.ctx_id != id) {
         void *p = nullptr;
         const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess || !p)
             return say(err, errlen, DS_ERR_CUDA, "cudaGetSymbolAddress: %s", cudaGetErrorString(e));
-        g_addr[dev] = (unsigned char *)p;
+        c.addr = (unsigned char *)p;
+        c.ctx_id = id;
+        c.have_id = have_id;
     }
-    *out = g_addr[dev];
+    *out = c.addr;
     return DS_OK;
+}
+
+// the caller's per-site inputs, passed by value to the kernel that writes them into the scratch
+struct SiteInputs {
+    int nsite;
+    int has_mean;
+    double frac[3 * kMaxSites];
+    int site_of[kMaxSites];
+    float scat[kMaxSites];
+    double mean[kMaxSites];
+};
+
+__global__ void k_noalloc_sites(const SiteInputs in, double *sites, int *site_of, float *scat, double *mean) {
+    const int i = threadIdx.x;
+    if (i >= in.nsite) return;
+    for (int a = 0; a < 3; ++a) sites[3 * i + a] = in.frac[3 * i + a];
+    site_of[i] = in.site_of[i];
+    scat[i] = in.scat[i];
+    if (in.has_mean) mean[i] = in.mean[i];
 }
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -78,7 +132,13 @@ extern "C" ds_status ds_occupancy_intensity_noalloc(const double lattice[6], int
     using C = c_t<float>;
     if (err && errlen) err[0] = 0;
     if (!lattice || !frac_xyz || !occ_dev || !grid || !out_dev) return say(err, errlen, DS_ERR_ARG, "null argument");
-    if (nsite < 1 || nsite > 32) return say(err, errlen, DS_ERR_ARG, "nsite must be 1..32");
+    if (nsite < 1 || nsite > kMaxSites) return say(err, errlen, DS_ERR_ARG, "nsite must be 1..%d", kMaxSites);
+    for (int i = 0; i < nsite; ++i) {
+        for (int a = 0; a < 3; ++a)
+            if (!std::isfinite(frac_xyz[3 * i + a])) return say(err, errlen, DS_ERR_ARG, "site %d coordinate", i);
+        if (scat_len && !std::isfinite(scat_len[i])) return say(err, errlen, DS_ERR_ARG, "site %d scattering length", i);
+        if (mean_occ && !std::isfinite(mean_occ[i])) return say(err, errlen, DS_ERR_ARG, "site %d mean occupancy", i);
+    }
     if (nmodels < 1) return say(err, errlen, DS_ERR_ARG, "nmodels must be >= 1");
     if (mode != DS_TOTAL && mode != DS_DIFFUSE) return say(err, errlen, DS_ERR_ARG, "mode");
     const int n[3] = {n1, n2, n3};
@@ -152,7 +212,8 @@ extern "C" ds_status ds_occupancy_intensity_noalloc(const double lattice[6], int
                    (unsigned)DS_NOALLOC_SCRATCH_BYTES);
 
     int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) return say(err, errlen, DS_ERR_CUDA, "cudaGetDevice failed");
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaSetDevice(dev) != cudaSuccess)
+        return say(err, errlen, DS_ERR_CUDA, "no current CUDA device");
     unsigned char *base = nullptr;
     ds_status rc = scratch_address(dev, &base, err, errlen);
     if (rc != DS_OK) return rc;
@@ -164,12 +225,18 @@ extern "C" ds_status ds_occupancy_intensity_noalloc(const double lattice[6], int
     int *d_site_of = (int *)(base + o_site_of);
     float *d_scat = (float *)(base + o_scat);
     double *d_mean = (double *)(base + o_mean);
-    std::vector<float> scat(nsite, 1.0f);
-    if (scat_len)
-        for (int i = 0; i < nsite; ++i) scat[i] = (float)scat_len[i];
-    cudaMemcpyAsync(d_sites, frac_xyz, sizeof(double) * 3 * nsite, cudaMemcpyHostToDevice, st);
-    cudaMemcpyAsync(d_site_of, site_of.data(), sizeof(int) * nsite, cudaMemcpyHostToDevice, st);
-    cudaMemcpyAsync(d_scat, scat.data(), sizeof(float) * nsite, cudaMemcpyHostToDevice, st);
+    SiteInputs in;
+    memset(&in, 0, sizeof(in));
+    in.nsite = nsite;
+    in.has_mean = mean_occ != nullptr;
+    for (int i = 0; i < nsite; ++i) {
+        for (int a = 0; a < 3; ++a) in.frac[3 * i + a] = frac_xyz[3 * i + a];
+        in.site_of[i] = site_of[i];
+        in.scat[i] = scat_len ? (float)scat_len[i] : 1.0f;
+        in.mean[i] = mean_occ ? mean_occ[i] : 0.0;
+    }
+    k_noalloc_sites<<<1, kMaxSites, 0, st>>>(in, d_sites, d_site_of, d_scat, d_mean);
+    count_launches(1);
     for (int a = 0; a < 3; ++a) make_twiddles<float>(n[a], W[a], st);
 
     p.g = g;
@@ -198,10 +265,7 @@ extern "C" ds_status ds_occupancy_intensity_noalloc(const double lattice[6], int
     src.diffuse = p.diffuse;
     src.occ = occ_dev;
     src.mean = d_mean;
-    if (p.diffuse) {
-        if (mean_occ) cudaMemcpyAsync(d_mean, mean_occ, sizeof(double) * nsite, cudaMemcpyHostToDevice, st);
-        else site_means_occ(nmodels, nsite, g.ncell, occ_dev, d_mean, st);
-    }
+    if (p.diffuse && !mean_occ) site_means_occ(nmodels, nsite, g.ncell, occ_dev, d_mean, st);
     C *spec = (C *)(base + o_spec);
     C *work = (C *)(base + o_work);
     for (int f0 = 0; f0 < nf; f0 += fb)

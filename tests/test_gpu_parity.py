@@ -759,6 +759,9 @@ def test_perovskite_64cubed_displacive_full_size():
     torch.cuda.synchronize()
     peak = float(out.max())
     P = info["taylor_order"]
+    # the order chosen by the library is the oracle's: the smallest order whose remainder bound
+    # x_max^(P+1)/(P+1)! <= eps, x_max over the atoms and the corners of the whole grid
+    assert P == core.taylor_order(core.x_max(m, m.qgrid), 1e-5)
     idx = np.random.default_rng(11).choice(m.qgrid.nvox, 40, replace=False)
     hkl = sample_G(m, idx) / 64.0
     I_dir, F = core.displacive_intensity_direct(m, hkl, 1, return_F=True)
@@ -777,6 +780,50 @@ def test_perovskite_64cubed_displacive_full_size():
     want = noise.lanczos_resample(IG, Q.astype(np.float64), 2, 8)
     got = np.array([float(sm[tuple(p)]) for p in pick])
     assert np.all(np.abs(got - want) <= 1e-5 * float(sm.max()) + 1e-4 * np.abs(want))
+
+
+def test_perovskite_64cubed_fp32_against_fp64_on_corner_and_centre_zones():
+    """The perovskite 64^3 model (1,310,720 atoms, x_max ~ 8.6 on |h,k,l| <= 8, where the
+    alternating Taylor terms cancel most) at the oracle's order for eps = 1e-5 over the whole
+    grid: on every voxel of the two |Q|-maximal corner zones H = (7, 7, 7) (voxels up to
+    h = 7 + 63/64) and H = (-8, -8, -8) (down to h = -8), and of the centre zone H = (0, 0, 0),
+    the FP32 path is within 1e-5 of peak of the FP64 path with the same P; 420 voxels of those
+    zones (the Bragg position and the outermost corner of each included) are within the per-voxel
+    remainder bound of Section III C (+ 1e-5 of peak) of the exact direct sum, on both paths."""
+    import torch
+    m = syn.perovskite_correlated()
+    lm = to_library(ctx_holder(), m)
+    P = core.taylor_order(core.x_max(m, m.qgrid), 1e-5)
+    assert P >= 25
+    zones = [(7, 7, 7), (-8, -8, -8), (0, 0, 0)]
+    n = m.cells[0]
+    got = {}
+    for H in zones:
+        q = (tuple(float(h) for h in H), (1.0 / n,) * 3, (n, n, n))
+        for prec, dt in ((0, torch.float64), (1, torch.float32)):
+            o = torch.empty((n, n, n), dtype=dt, device="cuda")
+            _, info = lm.intensity(q, out=o, disorder=2, mode=1, precision=prec, taylor_order=P)
+            assert info["taylor_order"] == P
+            got[H, prec] = o
+        torch.cuda.synchronize()
+    peak = max(float(got[H, 0].max()) for H in zones)
+    for H in zones:
+        err = float((got[H, 1].double() - got[H, 0]).abs().max()) / peak
+        assert err < 1e-5, (H, err)
+    rng = np.random.default_rng(21)
+    G, vals = [], {0: [], 1: []}
+    for H in zones:
+        ijk = np.concatenate([rng.integers(0, n, (138, 3)), [[0, 0, 0], [n - 1, n - 1, n - 1]]])
+        G.append(np.asarray(H)[None, :] * n + ijk)
+        sel = torch.from_numpy(np.ravel_multi_index(ijk.T, (n, n, n))).cuda()
+        for prec in (0, 1):
+            vals[prec].append(got[H, prec].reshape(-1)[sel].double().cpu().numpy())
+    hkl = np.concatenate(G) / float(n)
+    I_dir, F = core.displacive_intensity_direct(m, hkl, 1, return_F=True)
+    bound = core.truncation_bound(m, hkl, P, 1, F=F, chunk=32)
+    for prec in (0, 1):
+        v = np.concatenate(vals[prec])
+        assert np.all(np.abs(v - I_dir) <= bound + 1e-5 * peak), prec
 
 
 def test_subbox_random_displacive_fcc32_plane_full_size():

@@ -96,3 +96,31 @@ def test_bounded_wait_and_poll_while_paused():
     with pytest.raises(ds.DSError):
         lm.submit(qgrid_tuple(m.qgrid), out, disorder=1)   # no spins uploaded
     ctx.close()
+
+
+def test_served_and_direct_displacive_requests_on_one_model_concurrently():
+    """Displacive requests with several Taylor orders go through ds_submit (planned on the
+    serving worker thread) while the caller thread runs ds_request_intensity on the same model
+    with other orders: both threads fill the model's per-order table caches at the same time.
+    Every result equals the same request run alone."""
+    import torch
+    import paper_1809_07088_gb300 as ds
+    ctx = ds.Context(0)
+    m = syn.small_case(syn.DISP, cells=(8, 6, 8), nsite=3, nmodels=1, seed=340, sigma=0.08)
+    lm = to_library(ctx, m)
+    q = qgrid_tuple(m.qgrid)
+    served_P, direct_P = [3, 4, 5, 6, 7, 8], [9, 10, 11, 12]
+    base = dict(disorder=2, mode=1, precision=1)
+    # isolated results on a second model (empty caches), so the concurrent run builds its own
+    ref = to_library(ctx, m)
+    alone = {P: ref.intensity(q, taylor_order=P, **base)[0] for P in served_P + direct_P}
+    outs = [torch.full(m.qgrid.count, float("nan"), dtype=torch.float32, device="cuda") for _ in served_P]
+    tickets = [lm.submit(q, o, taylor_order=P, **base) for o, P in zip(outs, served_P)]
+    direct = {P: lm.intensity(q, taylor_order=P, **base)[0] for P in direct_P}
+    for t in tickets:
+        ctx.wait(t, 120.0)
+    for o, P in zip(outs, served_P):
+        assert np.array_equal(o.cpu().numpy(), alone[P]), P
+    for P in direct_P:
+        assert np.array_equal(direct[P], alone[P]), P
+    ctx.close()

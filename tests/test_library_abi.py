@@ -57,3 +57,29 @@ def test_create_without_gpu_fails_cleanly():
     st = lib.ds_create(ctypes.byref(h), 0, 0)
     assert st != 0 and not h.value
     assert lib.ds_version().decode().startswith("paper_1809_07088_gb300")
+
+
+def test_noalloc_rejects_non_finite_site_data_before_any_gpu_work():
+    """The allocation-free entry point checks its host arguments before touching the GPU: a NaN
+    coordinate, scattering length or mean occupancy is DS_ERR_ARG with a message (the device
+    pointers are never dereferenced, so placeholders are enough)."""
+    import numpy as np
+    from paper_1809_07088_gb300 import _binding as B
+    lib = B.load()
+    lat = (ctypes.c_double * 6)(4.0, 4.0, 4.0, 90.0, 90.0, 90.0)
+    q = B.make_qgrid((0.0, 0.0, 0.0), (0.25, 0.25, 0.25), (5, 5, 5))
+    fake_dev = ctypes.c_void_p(256)
+    good = np.array([[0.0, 0.0, 0.0], [0.5, 0.5, 0.5]])
+    for what in ("coord", "scat", "mean"):
+        sites, scat, mean = good.copy(), np.ones(2), np.full(2, 0.5)
+        if what == "coord":
+            sites[1, 2] = np.nan
+        elif what == "scat":
+            scat[0] = np.inf
+        else:
+            mean[1] = np.nan
+        err = ctypes.create_string_buffer(256)
+        st = lib.ds_occupancy_intensity_noalloc(lat, 2, sites.ctypes.data, scat.ctypes.data, 4, 4, 4, 1, fake_dev,
+                                                mean.ctypes.data, ctypes.byref(q), 1, fake_dev, None, err, len(err))
+        assert st == B.DS_ERR_ARG, what
+        assert "site" in err.value.decode()

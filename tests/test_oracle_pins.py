@@ -215,6 +215,30 @@ def test_lattice_fft_matches_brute_force_dft():
     assert abs(P[k0] - 60) < 1e-10 and np.abs(P).sum() - 60 < 1e-9
 
 
+@pytest.mark.parametrize("shape", [(7, 20, 32), (32, 7, 20), (20, 32, 7)])
+def test_lattice_fft_at_the_kernel_sizes_matches_separable_dft(shape):
+    """Eq. fft at the sizes the GPU transforms specialise (radix 7, 20 = 4 * 5, 32 = 4 * 4 * 2),
+    each size on each axis: the oracle's transform equals the definition evaluated one axis at
+    a time, X = sum_R x_R prod_a exp(2 pi i k_a R_a / n_a), with the phase of each 1-D matrix
+    reduced exactly (k R mod n in integers) before the exponential."""
+    rng = np.random.default_rng(sum(shape))
+    x = rng.standard_normal(shape) + 1j * rng.standard_normal(shape)
+    mats = []
+    for n in shape:
+        kR = np.mod(np.outer(np.arange(n), np.arange(n)), n)
+        mats.append(np.exp(2j * np.pi * kR / n))
+    want = np.einsum("ai,bj,ck,ijk->abc", mats[0], mats[1], mats[2], x)
+    got = core.lattice_fft(x)
+    assert np.max(np.abs(got - want)) < 1e-10 * np.max(np.abs(want))
+    # a plane wave exp(-2 pi i k0.R/n) lands in the single bin k0 with weight n1 n2 n3
+    k0 = tuple(n - 2 for n in shape)
+    R = np.stack(np.meshgrid(*(np.arange(n) for n in shape), indexing="ij"), -1)
+    pw = np.exp(-2j * np.pi * sum(k0[a] * R[..., a] / shape[a] for a in range(3)))
+    P = core.lattice_fft(pw)
+    N = float(np.prod(shape))
+    assert abs(P[k0] - N) < 1e-9 * N and np.abs(P).sum() - N < 1e-8 * N
+
+
 def test_parseval():
     """sum_k |X_k|^2 = n1 n2 n3 sum_R |x_R|^2 for every transformed field."""
     rng = np.random.default_rng(2)

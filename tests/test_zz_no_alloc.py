@@ -5,7 +5,8 @@ framework that owns the GPU's memory through its own allocator, a process under 
 cap, a refinement loop that must not touch the allocator).  It keeps all its scratch in one
 static device array, so these tests check that two calls in a row -- the second on a different
 model, so stale scratch from the first would show -- agree with the ordinary entry point
-ds_request_intensity, and that an oversized request is refused before any work is queued.
+ds_request_intensity, that a call on a grid of many zones with ragged edges agrees with the CPU
+oracle, and that an oversized request is refused before any work is queued.
 
 This file is named to be collected last.
 """
@@ -29,7 +30,7 @@ def _const_ff_model(cells, nsite, nmodels, seed, sites=None):
     return m
 
 
-def _noalloc(lib, m, mode, out, stream):
+def _noalloc(lib, m, mode, out, stream, mean=None):
     import paper_1809_07088_gb300._binding as B
     import torch
     occ = torch.from_numpy(np.ascontiguousarray(m.occ)).cuda()
@@ -38,8 +39,12 @@ def _noalloc(lib, m, mode, out, stream):
     scat = np.ascontiguousarray(m.scat_len, dtype=np.float64)
     q = B.make_qgrid(*qgrid_tuple(m.qgrid))
     err = ctypes.create_string_buffer(512)
+    mean_p = None
+    if mean is not None:
+        mean = np.ascontiguousarray(mean, dtype=np.float64)
+        mean_p = mean.ctypes.data
     st = lib.ds_occupancy_intensity_noalloc(lat, m.nsite, sites.ctypes.data, scat.ctypes.data, *m.cells,
-                                            m.nmodels, occ.data_ptr(), None, ctypes.byref(q), mode,
+                                            m.nmodels, occ.data_ptr(), mean_p, ctypes.byref(q), mode,
                                             out.data_ptr(), stream, err, len(err))
     return st, err.value.decode(), occ
 
@@ -67,6 +72,29 @@ def test_noalloc_matches_ordinary_entry_point_twice():
         assert np.isfinite(got).all()
         assert rel_err_of_peak(got, want) < TOL["fp32"]
     ctx.close()
+
+
+def test_noalloc_ragged_multizone_grid_against_oracle():
+    """A grid spanning 4 x 5 x 6 zones with ragged edges on every side (not a multiple of the
+    supercell), DIFFUSE with a caller-given mean and TOTAL, against the oracle's FFT method."""
+    import torch
+    import paper_1809_07088_gb300 as ds
+    from oracle import core
+    torch.cuda.set_device(0)
+    lib = ds.load()
+    stream = torch.cuda.current_stream().cuda_stream
+    m = _const_ff_model((5, 6, 4), 5, 2, 204)
+    n = m.cells
+    m.qgrid = syn.QGrid(h0=tuple(-1.0 - 3.0 / c for c in n), step=tuple(1.0 / c for c in n),
+                        count=(3 * n[0] + 7, 4 * n[1] + 1, 5 * n[2] + 3))
+    for mode, mean in ((ds.DS_DIFFUSE, np.array([0.3, 0.5, 0.45, 0.6, 0.2])), (ds.DS_TOTAL, None)):
+        m.mean_occ = mean
+        want = core.occupancy_intensity_fft(m, m.qgrid.g_index(m.cells), mode)
+        out = torch.full(m.qgrid.count, float("nan"), dtype=torch.float32, device="cuda")
+        st, msg, occ = _noalloc(lib, m, mode, out, stream, mean=mean)
+        assert st == 0, msg
+        torch.cuda.synchronize()
+        assert rel_err_of_peak(out.cpu().numpy(), want) < TOL["fp32"]
 
 
 def test_noalloc_rejects_oversized_request():
