@@ -99,7 +99,15 @@ typedef struct {
                            even part: the mean over lattice points and supercells of cos(G.u)),
                            the only coupling of moments and displacements the paper keeps;
                            0 = T = 1.  Not with DS_SMOOTH_SUBBOX, not accepted by ds_backward. */
+    int taylor_kernel;  /* displacive: how the Taylor sum of Eq. total_sf_taylor is evaluated (same sum,
+                           reordered): DS_TAYLOR_AUTO picks the cheaper of the two by a cost model;
+                           DS_TAYLOR_PER_VOXEL sums the monomials voxel by voxel; DS_TAYLOR_SUM_FACTORISED
+                           evaluates, for every k, the polynomial in the r.l.u. coordinates over all zones
+                           at once, one axis at a time (one order for the grid; DS_ERR_UNSUPPORTED when a
+                           k's box of zones is wider than 17 along an axis, or with taylor_zonal). */
 } ds_opts;
+
+enum { DS_TAYLOR_AUTO = 0, DS_TAYLOR_PER_VOXEL = 1, DS_TAYLOR_SUM_FACTORISED = 2 };
 
 typedef struct {
     int taylor_order;        /* P used (displacive), else 0 */

@@ -13,11 +13,12 @@ import numpy as np
 
 from ._binding import (DS_DIFFUSE, DS_DISP, DS_FF_CONST, DS_FF_GAUSS4, DS_FF_J0, DS_FP32, DS_FP64,
                        DS_OCC, DS_SMOOTH_LANCZOS, DS_SMOOTH_NONE, DS_SMOOTH_SPHERE, DS_SMOOTH_SUBBOX, DS_SPIN,
-                       DS_TOTAL,
+                       DS_TAYLOR_AUTO, DS_TAYLOR_PER_VOXEL, DS_TAYLOR_SUM_FACTORISED, DS_TOTAL,
                        DSError, check, ds_result_info, load, make_opts, make_qgrid)
 
 __all__ = ["Context", "Model", "DSError", "load", "make_opts", "make_qgrid", "DS_OCC", "DS_SPIN",
-           "DS_DISP", "DS_TOTAL", "DS_DIFFUSE", "DS_FP32", "DS_FP64", "DS_SMOOTH_NONE",
+           "DS_DISP", "DS_TAYLOR_AUTO", "DS_TAYLOR_PER_VOXEL", "DS_TAYLOR_SUM_FACTORISED", "DS_TOTAL",
+           "DS_DIFFUSE", "DS_FP32", "DS_FP64", "DS_SMOOTH_NONE",
            "DS_SMOOTH_LANCZOS", "DS_SMOOTH_SUBBOX", "DS_SMOOTH_SPHERE", "DS_FF_CONST", "DS_FF_GAUSS4", "DS_FF_J0"]
 
 

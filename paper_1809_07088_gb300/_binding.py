@@ -18,6 +18,7 @@ DS_OCC, DS_SPIN, DS_DISP = 0, 1, 2
 DS_TOTAL, DS_DIFFUSE = 0, 1
 DS_FP64, DS_FP32 = 0, 1
 DS_SMOOTH_NONE, DS_SMOOTH_LANCZOS, DS_SMOOTH_SUBBOX, DS_SMOOTH_SPHERE = 0, 1, 2, 3
+DS_TAYLOR_AUTO, DS_TAYLOR_PER_VOXEL, DS_TAYLOR_SUM_FACTORISED = 0, 1, 2
 
 _STATUS = {0: "DS_OK", -1: "DS_ERR_ARG", -2: "DS_ERR_STATE", -3: "DS_ERR_OOM", -4: "DS_ERR_ADMISSION",
            -5: "DS_ERR_TIMEOUT", -6: "DS_ERR_CUDA", -7: "DS_ERR_UNSUPPORTED"}
@@ -31,7 +32,7 @@ class ds_opts(C.Structure):
     _fields_ = [("disorder", C.c_int), ("mode", C.c_int), ("precision", C.c_int),
                 ("taylor_order", C.c_int), ("taylor_eps", C.c_double), ("smoothing", C.c_int),
                 ("lanczos_m", C.c_int), ("lanczos_mprime", C.c_int), ("subbox_n", C.c_int),
-                ("taylor_zonal", C.c_int), ("dw_coupling", C.c_int)]
+                ("taylor_zonal", C.c_int), ("dw_coupling", C.c_int), ("taylor_kernel", C.c_int)]
 
 
 class ds_result_info(C.Structure):
@@ -120,7 +121,7 @@ def make_qgrid(h0, step, count) -> ds_qgrid:
 
 def make_opts(disorder, mode=DS_DIFFUSE, precision=DS_FP32, taylor_order=-1, taylor_eps=1e-8,
               smoothing=DS_SMOOTH_NONE, lanczos_m=2, lanczos_mprime=2, subbox_n=1,
-              taylor_zonal=0, dw_coupling=0) -> ds_opts:
+              taylor_zonal=0, dw_coupling=0, taylor_kernel=0) -> ds_opts:
     o = ds_opts()
     o.disorder, o.mode, o.precision = int(disorder), int(mode), int(precision)
     o.taylor_order, o.taylor_eps = int(taylor_order), float(taylor_eps)
@@ -128,4 +129,5 @@ def make_opts(disorder, mode=DS_DIFFUSE, precision=DS_FP32, taylor_order=-1, tay
         int(lanczos_mprime), int(subbox_n)
     o.taylor_zonal = int(taylor_zonal)
     o.dw_coupling = int(dw_coupling)
+    o.taylor_kernel = int(taylor_kernel)
     return o

@@ -3,12 +3,14 @@
 // The paper has no adjoint; this is the chain rule of its forward equations, TOTAL mode.
 //
 // Displacive.  F_m(G) = sum_mu phi_mu(G) sum_t c_t(G) M'_{m,mu,t}(k) with the stored transforms
-// M' = i^n FFT(field_t), field_t = w (u~x^a/a!)(u~y^b/b!)(u~z^c/c!), u~ = u Qs, c_t = (Q/Qs)^t and
+// M' = i^n FFT(field_t), field_t = w (v1^a/a!)(v2^b/b!)(v3^c/c!), v_j = gs_j b*_j . u (the
+// displacement on the reciprocal axes, scaled), c_t = x1^a x2^b x3^c with x_j = g_j / gs_j, and
 // I = sum_m |F_m|^2 / (M N).  Hence
 //     dL/dfield_{m,mu,t}(R) = Re[ i^n sum_k exp(ik.R) Z_{m,mu,t}(k) ],
 //     Z_{m,mu,t}(k) = (2/(M N)) sum_{H: H+k in grid} dL/dI(G) conj(F_m(G)) phi_mu(G) c_t(G),
-//     dL/du_alpha(R) = Qs w sum_t dL/dfield_t(R) field_{t - e_alpha}(R) / w,
-// because d(u~^a/a!)/du = Qs u~^(a-1)/(a-1)!.  Magnetic: I = C sum_m F^H P F / (M N) with
+//     dL/dv_j(R) = w sum_t dL/dfield_t(R) field_{t - e_j}(R) / w,
+//     dL/du_alpha(R) = sum_j gs_j b*_{j,alpha} dL/dv_j(R),
+// because d(v^a/a!)/dv = v^(a-1)/(a-1)!.  Magnetic: I = C sum_m F^H P F / (M N) with
 // P = 1 - G^ G^T (2/3 at G = 0), so dL/dM_{m,mu,alpha}(R) = Re[sum_k exp(ik.R) Z_{m,mu,alpha}(k)],
 // Z = (2C/(M N)) sum_H dL/dI conj((P F)_alpha) phi_mu.
 //
@@ -181,7 +183,7 @@ __global__ void __launch_bounds__(256) k_adj_z_disp(const __grid_constant__ Reco
                 Qd[a] = (double)G[0] / g.n[0] * p.recip[a] + (double)G[1] / g.n[1] * p.recip[3 + a] +
                         (double)G[2] / g.n[2] * p.recip[6 + a];
             if (part < 3) {
-                const T qs = (T)(Qd[part] / p.qscale);  // |qs| <= 1
+                const T qs = (T)((double)G[part] / g.n[part] / p.gscale[part]);  // x_part, |x| <= 1
                 T *dst = pw + ((size_t)zi * 3 + part) * (P + 1);
                 T v = T(1);
                 for (int q = 0; q <= P; ++q) {
@@ -292,10 +294,14 @@ __global__ void k_adj_z_mag(const __grid_constant__ RecombParams<T> p, const T *
     Z[(((size_t)p.model * p.nsite + site) * 3 + alpha) * g.ncell + k] = acc;
 }
 
-// grad[m][mu][cell][alpha] = Qs w sum_t D_t(cell) field_{t - e_alpha}(cell) / w
+// grad[m][mu][cell][alpha] = sum_j gs_j b*_{j,alpha} w sum_t D_t(cell) field_{t - e_j}(cell) / w
+struct GradAxes {
+    double bg[9];  // gs_j b*_{j,alpha}, row j
+};
+
 template <typename T>
 __global__ void k_adj_gather(int nmodels, int nsite, int ncell, int P, int nT, const int4 *terms, const T *pw,
-                             const uint8_t *occ, const T *D, double qscale, T *grad) {
+                             const uint8_t *occ, const T *D, const GradAxes ax, T *grad) {
     const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     const size_t natom = (size_t)nmodels * nsite * ncell;
     if (idx >= natom) return;
@@ -314,10 +320,10 @@ __global__ void k_adj_gather(int nmodels, int nsite, int ncell, int P, int nT, c
         if (e.y > 0) gy = fma(dv, ax * py[(size_t)(e.y - 1) * ncell] * cz, gy);
         if (e.z > 0) gz = fma(dv, ax * by * pz[(size_t)(e.z - 1) * ncell], gz);
     }
-    const T w = (T)qscale * (occ ? (T)occ[idx] : T(1));
-    grad[idx * 3 + 0] = w * gx;
-    grad[idx * 3 + 1] = w * gy;
-    grad[idx * 3 + 2] = w * gz;
+    const T w = occ ? (T)occ[idx] : T(1);
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+        grad[idx * 3 + a] = w * ((T)ax.bg[a] * gx + (T)ax.bg[3 + a] * gy + (T)ax.bg[6 + a] * gz);
 }
 
 template <typename T>
@@ -405,9 +411,12 @@ ds_status backward_run(ds_model *M, const ds_qgrid *q, const ds_opts *o, const T
         if (mag) {
             k_mag_grad_layout<T><<<(unsigned)((natom * 3 + 255) / 256), 256, 0, st>>>(nmod, nsite, g.ncell, D, grad);
         } else {
+            GradAxes ax;
+            for (int j = 0; j < 3; ++j)
+                for (int a = 0; a < 3; ++a) ax.bg[3 * j + a] = p.gscale[j] * p.recip[3 * j + a];
             k_adj_gather<T><<<(unsigned)((natom + 255) / 256), 256, 0, st>>>(
                 nmod, nsite, g.ncell, keep.src.P, nT, keep.terms, keep.pw, M->has_occ ? M->d_occ : nullptr, D,
-                p.qscale, grad);
+                ax, grad);
         }
         count_launches(1);
     }

@@ -646,6 +646,10 @@ ds_status check_request(ds_model *M, const ds_qgrid *q, const ds_opts *o) {
     if (o->disorder == DS_DISP && o->taylor_order > 60) return ds_fail(ctx, DS_ERR_UNSUPPORTED, "taylor_order > 60");
     if (o->taylor_zonal != 0 && o->taylor_zonal != 1) return ds_fail(ctx, DS_ERR_ARG, "taylor_zonal must be 0 or 1");
     if (o->dw_coupling != 0 && o->dw_coupling != 1) return ds_fail(ctx, DS_ERR_ARG, "dw_coupling must be 0 or 1");
+    if (o->taylor_kernel < DS_TAYLOR_AUTO || o->taylor_kernel > DS_TAYLOR_SUM_FACTORISED)
+        return ds_fail(ctx, DS_ERR_ARG, "taylor_kernel");
+    if (o->taylor_kernel == DS_TAYLOR_SUM_FACTORISED && o->taylor_zonal)
+        return ds_fail(ctx, DS_ERR_UNSUPPORTED, "the sum-factorised Taylor kernel uses one order for the grid");
     if (o->dw_coupling) {
         if (o->disorder != DS_SPIN)
             return ds_fail(ctx, DS_ERR_UNSUPPORTED, "dw_coupling applies to magnetic requests (Eq. mag_sf)");
@@ -917,11 +921,13 @@ ds_status plan_and_run(ds_model *M, const ds_qgrid *q, const ds_opts *o, T *d_ou
         src.mean = M->d_mean_spin;
         p.ncomp = 3;
     } else {
-        Corners corners;
-        box_corners(M, eg0, ecnt, corners.v);
-        double qscale = 0.0;
-        for (int i = 0; i < 24; ++i) qscale = std::max(qscale, fabs(corners.v[i]));
-        if (!(qscale > 0)) qscale = 1.0;
+        // coefficient scales: the largest |g_a| = |G_a| / n_a over the computing grid, so that the
+        // scaled coefficients x1^a x2^b x3^c stay within [-1, 1]
+        double gscale[3];
+        for (int a = 0; a < 3; ++a) {
+            gscale[a] = std::max(fabs((double)eg0[a]), fabs((double)eg0[a] + ecnt[a] - 1)) / g.n[a];
+            if (!(gscale[a] > 0)) gscale[a] = 1.0;
+        }
         P = o->taylor_order;
         double umax = 0.0;
         const bool auto_order = P < 0;
@@ -939,7 +945,7 @@ ds_status plan_and_run(ds_model *M, const ds_qgrid *q, const ds_opts *o, T *d_ou
         if (rc != DS_OK) return rc;
         T *pw = (T *)ws.get(sizeof(T) * natom * 3 * (P + 1));
         if (ws.failed) return ds_fail(ctx, DS_ERR_OOM, "device allocation failed (power tables)");
-        make_powers<T>(g, nmod, nsite, P, qscale, M->d_disp, pw, st);
+        make_powers<T>(g, nmod, nsite, P, M->recip, gscale, M->d_disp, pw, st);
         src.kind = SRC_DISP;
         src.pw = pw;
         src.terms = d_terms;
@@ -951,7 +957,7 @@ ds_status plan_and_run(ds_model *M, const ds_qgrid *q, const ds_opts *o, T *d_ou
         p.nT = Tn;
         p.ops = d_ops;
         p.terms = d_terms;
-        p.qscale = qscale;
+        for (int a = 0; a < 3; ++a) p.gscale[a] = gscale[a];
         if (auto_order && o->taylor_zonal && P > 0) {
             // Taylor order per zone: every voxel G of a zone has max_j |Q.u_j| <= min(|Q|max u_max,
             // x_max) (Cauchy-Schwarz), so the remainder bound of Section III C holds there with the
@@ -1002,6 +1008,37 @@ ds_status plan_and_run(ds_model *M, const ds_qgrid *q, const ds_opts *o, T *d_ou
     src.nf_per_model = nf_model;
     const int nf = nf_model * nmod;
 
+    // displacive with one order for the grid: the sum-factorised recombination (taylor_sf.cu), with
+    // zone phases over the grid's zones and those of its negation (Friedel mates)
+    bool use_sf = false;
+    if (o->disorder == DS_DISP && !p.pzone && o->taylor_kernel != DS_TAYLOR_PER_VOXEL) {
+        std::vector<int4> items;
+        const bool force = o->taylor_kernel == DS_TAYLOR_SUM_FACTORISED;
+        const bool ok = taylor_sf_plan(g, gm, P, nsite, sizeof(C), force, p.sf, items);
+        if (force && !ok)
+            return ds_fail(ctx, DS_ERR_UNSUPPORTED, "sum-factorised Taylor kernel: zone boxes wider than 17 per axis");
+        if (ok) {
+            GridMap gmx = gm;
+            int nHx = 1;
+            for (int a = 0; a < 3; ++a) {
+                const int Hmax = gm.Hmin[a] + gm.nH[a] - 1;
+                gmx.Hmin[a] = std::min(gm.Hmin[a], -Hmax - 1);
+                gmx.nH[a] = std::max(Hmax, -gm.Hmin[a]) - gmx.Hmin[a] + 1;
+                nHx = std::max(nHx, gmx.nH[a]);
+            }
+            const C *phk2 = nullptr;
+            rc = site_tables<T>(M, g, gmx, p.nmax, nHx, st, ws, &phk2, &p.phHx);
+            if (rc != DS_OK) return rc;
+            for (int a = 0; a < 3; ++a) p.Hminx[a] = gmx.Hmin[a];
+            p.nHx = nHx;
+            int4 *d_items = (int4 *)ws.get(sizeof(int4) * items.size());
+            if (ws.failed) return ds_fail(ctx, DS_ERR_OOM, "device allocation failed (Taylor plan)");
+            CK(cudaMemcpyAsync(d_items, items.data(), sizeof(int4) * items.size(), cudaMemcpyHostToDevice, st));
+            p.sf.items = d_items;
+            use_sf = true;
+        }
+    }
+
     // per-site transforms (Section III)
     C *spec = (C *)ws.get(sizeof(C) * (size_t)nf * g.ncell_h);
     const size_t work_cap = 512ull << 20;
@@ -1045,7 +1082,8 @@ ds_status plan_and_run(ds_model *M, const ds_qgrid *q, const ds_opts *o, T *d_ou
         for (int m = 0; m < nmod; ++m) {
             p.model = m;
             p.accumulate = m > 0;
-            recombine_disp<T>(p, st);
+            if (use_sf) recombine_disp_sf<T>(p, st);
+            else recombine_disp<T>(p, st);
         }
     } else {
         ProfScope ps(ctx, p.ncomp == 1 ? "recombine_occ" : "recombine_spin", st);

@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "ds_common.cuh"
 #include "fft_lines.cuh"
 
@@ -99,6 +101,20 @@ struct SiteGroups {
     int cls_grp_end[MAX_FF_CLASSES];   // exclusive end of each form-factor class (group index)
 };
 
+// plan of the sum-factorised Taylor recombination (taylor_sf.cu): the monomial exponents a are
+// processed in groups (shared-memory budget), each group's (a, b) pairs listed in a balanced order
+constexpr int SF_MAX_GROUPS = 24;
+struct SFPlan {
+    int zr;                            // register width: zones per axis of a CTA's box (<= zr)
+    int ngroups;
+    int a0[SF_MAX_GROUPS + 1];         // group g holds a in [a0[g], a0[g+1])
+    int ibeg[SF_MAX_GROUPS + 1];       // its slots in `items`: [ibeg[g], ibeg[g+1])
+    int xpad;                          // row stride of the per-group partial sums X[h3][item]
+    int ymax;                          // largest group (a values)
+    size_t smem;                       // dynamic shared memory of one CTA
+    const int4 *items;                 // slots: (a, b, t0, xi), a < 0 = empty slot
+};
+
 template <typename T> struct RecombParams {
     Geometry g;
     GridMap gm;
@@ -118,7 +134,9 @@ template <typename T> struct RecombParams {
     SiteGroups grp;
     double recip[9];                    // a*, b*, c* rows (1/A)
     T qstep[9];                         // a*/n1, b*/n2, c*/n3 rows: Q = sum_a G_a qstep_a
-    double qscale;                      // displacive: coefficient uses Q / qscale
+    double gscale[3];                   // displacive: coefficients use x_a = g_a / gscale_a, g_a = G_a / n_a
+    const c_t<T> *phHx;                 // displacive: exp(2 pi i H_a r_a) [site][3][nHx] over the zones of
+    int Hminx[3], nHx;                  //   the grid and of its negation (Friedel mates), from zone Hminx
     T norm;                             // 1/(nmodels N), times C for magnetic
     const int *ops;                     // displacive coefficient update codes per monomial
     const int4 *terms;                  // displacive monomials (a, b, c, n)
@@ -132,6 +150,7 @@ template <typename T> struct RecombParams {
     int force_plain;                    // use the per-site (ungrouped) recombination
     int dres[3];                        // residue classes of zones per axis (0: per-zone kernels)
     const T *dw;                        // optional: Debye-Waller factor T_mu(G) [site][voxel] (magnetic)
+    SFPlan sf;                          // displacive, sum-factorised recombination
     int *err;
 };
 
@@ -154,9 +173,10 @@ size_t fft_work_bytes(const Geometry &g, int nf, size_t elem);
 template <typename T>
 void make_site_tables(const Geometry &g, const GridMap &gm, int nsite, const double *sites_dev,
                       c_t<T> *phk, c_t<T> *phH, int nmax, int nHmax, cudaStream_t s);
+// pw[m][s][a][e][cell] = (gscale_a u~_a)^e / e!, u~_a = b*_a . u (recip rows b*_a, Cartesian)
 template <typename T>
-void make_powers(const Geometry &g, int nmodels, int nsite, int P, double qscale, const float *disp,
-                 T *pw, cudaStream_t s);
+void make_powers(const Geometry &g, int nmodels, int nsite, int P, const double recip[9], const double gscale[3],
+                 const float *disp, T *pw, cudaStream_t s);
 void site_means_occ(int nmodels, int nsite, int ncell, const uint8_t *occ, double *mean, cudaStream_t s);
 void site_means_spin(int nmodels, int nsite, int ncell, const float *spins, double *mean, cudaStream_t s);
 struct Corners {
@@ -168,6 +188,14 @@ template <typename T> void recombine_cm(const RecombParams<T> &p, cudaStream_t s
 // recomb_res.cu: the residue-class kernel when p.dres is set; false when it does not apply
 template <typename T> bool recombine_cm_residues(const RecombParams<T> &p, cudaStream_t s);
 template <typename T> void recombine_disp(const RecombParams<T> &p, cudaStream_t s);
+// taylor_sf.cu: the displacive recombination by sum factorisation over the zones of each k (one
+// Taylor order for the grid); false when it does not apply (zone orders, zone boxes too large)
+template <typename T> void recombine_disp_sf(const RecombParams<T> &p, cudaStream_t s);
+// host plan of that kernel (false: zone boxes wider than it handles, or, unless forced, more work
+// than the per-voxel recombination); `items` is the slot table to upload, its device address then
+// goes into plan.items
+bool taylor_sf_plan(const Geometry &g, const GridMap &gm, int P, int nsite, size_t celem, bool force, SFPlan &plan,
+                    std::vector<int4> &items);
 template <typename T>
 void displacive_bragg(const RecombParams<T> &p, const int4 *terms, c_t<T> *avg0, c_t<T> *bragg, cudaStream_t s);
 

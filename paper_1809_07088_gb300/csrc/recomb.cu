@@ -54,16 +54,25 @@ void make_site_tables(const Geometry &g, const GridMap &gm, int nsite, const dou
     count_launches(1);
 }
 
-// pw[m][s][a][e][cell] = (u_a Qs)^e / e!, built by the recurrence p_e = p_{e-1} u~ / e in FP64
+// pw[m][s][a][e][cell] = (gs_a u~_a)^e / e! with u~_a = b*_a . u the displacement projected on the
+// reciprocal vector b*_a (so that Q.u = sum_a g_a u~_a for Q = sum_a g_a b*_a, Section III C), built by
+// the recurrence p_e = p_{e-1} gs_a u~_a / e in FP64
+struct PowerAxes {
+    double b[9];   // rows b*_a (Cartesian, 1/A, including 2 pi)
+    double gs[3];  // per-axis scales of the coefficients
+};
+
 template <typename T>
-__global__ void k_powers(int nmodels, int nsite, int ncell, int P, double qscale, const float *disp, T *pw) {
+__global__ void k_powers(int nmodels, int nsite, int ncell, int P, const PowerAxes ax, const float *disp, T *pw) {
     const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     const size_t natom = (size_t)nmodels * nsite * ncell;
     if (idx >= natom * 3) return;
     const int a = (int)(idx / natom);
     const size_t atom = idx - (size_t)a * natom;        // (m, s, cell) linear
     const size_t ms = atom / ncell, cell = atom - ms * ncell;
-    const double u = (double)disp[atom * 3 + a] * qscale;
+    const double ut = ax.b[3 * a] * (double)disp[atom * 3] + ax.b[3 * a + 1] * (double)disp[atom * 3 + 1] +
+                      ax.b[3 * a + 2] * (double)disp[atom * 3 + 2];
+    const double u = ut * ax.gs[a];
     T *dst = pw + ((ms * 3 + a) * (size_t)(P + 1)) * ncell + cell;
     double p = 1.0;
     dst[0] = (T)1;
@@ -74,10 +83,13 @@ __global__ void k_powers(int nmodels, int nsite, int ncell, int P, double qscale
 }
 
 template <typename T>
-void make_powers(const Geometry &g, int nmodels, int nsite, int P, double qscale, const float *disp, T *pw,
-                 cudaStream_t s) {
+void make_powers(const Geometry &g, int nmodels, int nsite, int P, const double recip[9], const double gscale[3],
+                 const float *disp, T *pw, cudaStream_t s) {
+    PowerAxes ax;
+    for (int i = 0; i < 9; ++i) ax.b[i] = recip[i];
+    for (int a = 0; a < 3; ++a) ax.gs[a] = gscale[a];
     const size_t n = (size_t)nmodels * nsite * g.ncell * 3;
-    k_powers<T><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(nmodels, nsite, g.ncell, P, qscale, disp, pw);
+    k_powers<T><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(nmodels, nsite, g.ncell, P, ax, disp, pw);
     count_launches(1);
 }
 
@@ -170,6 +182,12 @@ __device__ __forceinline__ void q_of_G(const double *recip, const int *n, int G1
     const double h = (double)G1 / n[0], k = (double)G2 / n[1], l = (double)G3 / n[2];
 #pragma unroll
     for (int a = 0; a < 3; ++a) Q[a] = h * recip[a] + k * recip[3 + a] + l * recip[6 + a];
+}
+// scaled Taylor coefficients' variables x_a = (G_a / n_a) / gscale_a (|x_a| <= 1 on the grid)
+__device__ __forceinline__ void x_of_G(const double *gscale, const int *n, int G1, int G2, int G3, double *x) {
+    x[0] = (double)G1 / n[0] / gscale[0];
+    x[1] = (double)G2 / n[1] / gscale[1];
+    x[2] = (double)G3 / n[2] / gscale[2];
 }
 
 // ------------------------------------------------------------------------------------------
@@ -666,7 +684,8 @@ template <typename T> void recombine_cm(const RecombParams<T> &p, cudaStream_t s
 // The transforms M_mu,t(k) of the CTA's k are staged TC monomials at a time in shared memory
 // by asynchronous copies, double buffered (the next chunk is in flight while the current one is
 // used), and read by all lanes of a warp at once.  Each lane keeps the scaled coefficients
-// (Qx/Qs)^a (Qy/Qs)^b (Qz/Qs)^c of its ZPT voxels, updated with one multiply per monomial
+// x1^a x2^b x3^c (x_j = g_j / gs_j, g the r.l.u. coordinates of G) of its ZPT voxels, updated with
+// one multiply per monomial
 // (monomials run in lexicographic (a, b, c) order), and accumulates S_mu += coef * M_mu,t.
 // A k of the other half of the spectrum reads the stored i^n M(-k): its value is
 // (-1)^n conj(stored), applied with compile-time signs in a separate loop body.
@@ -829,11 +848,11 @@ __global__ void __launch_bounds__(DISP_KT * 32, MINB) k_recomb_disp(const __grid
     for (int j = 0; j < ZPT; ++j) {
         int Gj[3];
         voxel_G(j, Gj);
-        double Qd[3];
-        q_of_G(p.recip, g.n, Gj[0], Gj[1], Gj[2], Qd);
-        qx[j] = qsign * (T)(Qd[0] / p.qscale);
-        qy[j] = qsign * (T)(Qd[1] / p.qscale);
-        qz[j] = qsign * (T)(Qd[2] / p.qscale);
+        double Xd[3];
+        x_of_G(p.gscale, g.n, Gj[0], Gj[1], Gj[2], Xd);
+        qx[j] = qsign * (T)Xd[0];
+        qy[j] = qsign * (T)Xd[1];
+        qz[j] = qsign * (T)Xd[2];
         qzp[j] = pair_of(qz[j]);
         ca[j] = cb[j] = T(1);
         ccp[j] = pair_of(T(1));
@@ -938,7 +957,9 @@ __global__ void __launch_bounds__(DISP_KT * 32, MINB) k_recomb_disp(const __grid
         int Gj[3];
         voxel_G(j, Gj);
         const int G1 = Gj[0], G2 = Gj[1], G3 = Gj[2];
-        const T q2 = (T)(p.qscale * p.qscale) * (qx[j] * qx[j] + qy[j] * qy[j] + qz[j] * qz[j]);
+        double Qd[3];
+        q_of_G(p.recip, g.n, G1, G2, G3, Qd);
+        const T q2 = (T)(Qd[0] * Qd[0] + Qd[1] * Qd[1] + Qd[2] * Qd[2]);
         const T s2 = q2 * (T)(1.0 / (FOUR_PI_D * FOUR_PI_D));
         const int H1 = (G1 - k1) / g.n[0], H2 = (G2 - k2) / g.n[1], H3 = (G3 - k3) / g.n[2];
         const int h1 = H1 - gm.Hmin[0], h2 = H2 - gm.Hmin[1], h3 = H3 - gm.Hmin[2];
@@ -1026,9 +1047,10 @@ __global__ void k_bragg_disp(RecombParams<T> p, const c_t<T> *avg0, c_t<T> *brag
     if (z >= nz) return;
     const int h3 = z % gm.nH[2], h2 = (z / gm.nH[2]) % gm.nH[1], h1 = z / (gm.nH[2] * gm.nH[1]);
     const int G1 = p.g.n[0] * (gm.Hmin[0] + h1), G2 = p.g.n[1] * (gm.Hmin[1] + h2), G3 = p.g.n[2] * (gm.Hmin[2] + h3);
-    double Qd[3];
+    double Qd[3], Xd[3];
     q_of_G(p.recip, p.g.n, G1, G2, G3, Qd);
-    const double qx = Qd[0] / p.qscale, qy = Qd[1] / p.qscale, qz = Qd[2] / p.qscale;
+    x_of_G(p.gscale, p.g.n, G1, G2, G3, Xd);
+    const double qx = Xd[0], qy = Xd[1], qz = Xd[2];
     const T q2 = (T)(Qd[0] * Qd[0] + Qd[1] * Qd[1] + Qd[2] * Qd[2]);
     const T s2 = q2 * (T)(1.0 / (FOUR_PI_D * FOUR_PI_D));
     C F = mk<T>(T(0), T(0)), part = mk<T>(T(0), T(0));
@@ -1075,7 +1097,8 @@ void displacive_bragg(const RecombParams<T> &p, const int4 *terms, c_t<T> *avg0,
 #define DS_INST(T)                                                                                          \
     template void make_site_tables<T>(const Geometry &, const GridMap &, int, const double *, c_t<T> *,     \
                                       c_t<T> *, int, int, cudaStream_t);                                    \
-    template void make_powers<T>(const Geometry &, int, int, int, double, const float *, T *, cudaStream_t); \
+    template void make_powers<T>(const Geometry &, int, int, int, const double *, const double *, const float *, T *, \
+                                 cudaStream_t);                                                             \
     template void recombine_cm<T>(const RecombParams<T> &, cudaStream_t);                                   \
     template void recombine_disp<T>(const RecombParams<T> &, cudaStream_t);                                 \
     template void displacive_bragg<T>(const RecombParams<T> &, const int4 *, c_t<T> *, c_t<T> *, cudaStream_t);

@@ -53,13 +53,18 @@ def test_magnetic_small_triclinic(ctx, prec, tag, mode):
     assert rel_err_of_peak(got, want) < TOL[tag]
 
 
+KERNELS = [1, 2]   # the per-voxel and the sum-factorised evaluation of the Taylor sum
+
+
+@pytest.mark.parametrize("kern", KERNELS)
 @pytest.mark.parametrize("prec,tag", PREC)
 @pytest.mark.parametrize("mode", [0, 1])
-def test_displacive_small_with_occupancy(ctx, prec, tag, mode):
+def test_displacive_small_with_occupancy(ctx, prec, tag, mode, kern):
     m = syn.small_case(syn.DISP, cells=(4, 6, 5), nsite=3, nmodels=2, seed=103, sigma=0.05)
     lm = to_library(ctx, m)
     P = 7
-    got, info = lm.intensity(qgrid_tuple(m.qgrid), disorder=2, mode=mode, precision=prec, taylor_order=P)
+    got, info = lm.intensity(qgrid_tuple(m.qgrid), disorder=2, mode=mode, precision=prec, taylor_order=P,
+                             taylor_kernel=kern)
     assert info["taylor_order"] == P and info["n_monomials"] == (P + 1) * (P + 2) * (P + 3) // 6
     want = core.displacive_intensity_fft(m, _G(m), mode, P=P)
     assert rel_err_of_peak(got, want) < TOL[tag]
@@ -300,6 +305,28 @@ def test_errors_are_reported(ctx):
     with pytest.raises(ds.DSError) as e:
         lm.intensity(qgrid_tuple(m.qgrid), disorder=2)
     assert "DS_ERR_STATE" in str(e.value)
+
+
+def test_taylor_kernel_option_errors(ctx):
+    """The Taylor-kernel choice is validated: an unknown value, the sum-factorised kernel with zone
+    orders, and the sum-factorised kernel on a grid whose zone boxes are wider than 17 are refused."""
+    import paper_1809_07088_gb300 as ds
+    m = syn.small_case(syn.DISP, cells=(2, 2, 2), nsite=1, nmodels=1, seed=109, sigma=0.03)
+    lm = to_library(ctx, m)
+    q = qgrid_tuple(m.qgrid)
+    with pytest.raises(ds.DSError) as e:
+        lm.intensity(q, disorder=2, taylor_order=3, taylor_kernel=7)
+    assert "DS_ERR_ARG" in str(e.value)
+    with pytest.raises(ds.DSError) as e:
+        lm.intensity(q, disorder=2, taylor_order=-1, taylor_eps=1e-6, taylor_zonal=1, taylor_kernel=2)
+    assert "DS_ERR_UNSUPPORTED" in str(e.value)
+    wide = ((-10.0, -10.0, -10.0), (0.5, 0.5, 0.5), (41, 5, 5))   # 21 zones along the first axis
+    with pytest.raises(ds.DSError) as e:
+        lm.intensity(wide, disorder=2, taylor_order=3, taylor_kernel=2)
+    assert "DS_ERR_UNSUPPORTED" in str(e.value)
+    got, _ = lm.intensity(wide, disorder=2, mode=0, precision=0, taylor_order=3)
+    want = core.displacive_intensity_fft(m, syn.QGrid(*wide).g_index(m.cells), 0, P=3)
+    assert rel_err_of_peak(got, want) < TOL["fp64"]
 
 
 # ----------------------------------------------------------------------------------------------
@@ -626,8 +653,9 @@ def test_magnetic_debye_waller_errors(ctx):
 # adjoint
 # ----------------------------------------------------------------------------------------------
 
+@pytest.mark.parametrize("kern", KERNELS)
 @pytest.mark.parametrize("prec,tol", [(0, 1e-9), (1, 2e-4)])
-def test_displacive_gradient_against_oracle(ctx, prec, tol):
+def test_displacive_gradient_against_oracle(ctx, prec, tol, kern):
     """dchi^2/du through ds_backward (Taylor order high enough that truncation is below
     rounding) against the oracle's chain rule of the exact direct sum, TOTAL mode."""
     from oracle import adjoint
@@ -641,7 +669,7 @@ def test_displacive_gradient_against_oracle(ctx, prec, tol):
     lm = to_library(ctx, m)
     dt = np.float64 if prec == 0 else np.float32
     g = lm.backward(qgrid_tuple(m.qgrid), np.ascontiguousarray(dLdI, dtype=dt), disorder=2, mode=0,
-                    precision=prec, taylor_order=16)
+                    precision=prec, taylor_order=16, taylor_kernel=kern)
     assert g.shape == g_or.shape
     assert np.max(np.abs(g - g_or)) < tol * np.max(np.abs(g_or))
 
@@ -802,7 +830,8 @@ def test_perovskite_64cubed_fp32_against_fp64_on_corner_and_centre_zones():
         q = (tuple(float(h) for h in H), (1.0 / n,) * 3, (n, n, n))
         for prec, dt in ((0, torch.float64), (1, torch.float32)):
             o = torch.empty((n, n, n), dtype=dt, device="cuda")
-            _, info = lm.intensity(q, out=o, disorder=2, mode=1, precision=prec, taylor_order=P)
+            _, info = lm.intensity(q, out=o, disorder=2, mode=1, precision=prec, taylor_order=P,
+                                   taylor_kernel=1)
             assert info["taylor_order"] == P
             got[H, prec] = o
         torch.cuda.synchronize()
@@ -810,6 +839,12 @@ def test_perovskite_64cubed_fp32_against_fp64_on_corner_and_centre_zones():
     for H in zones:
         err = float((got[H, 1].double() - got[H, 0]).abs().max()) / peak
         assert err < 1e-5, (H, err)
+    # the sum-factorised kernel forced on the outermost zone (FP32) against the per-voxel FP64 path
+    q = ((7.0, 7.0, 7.0), (1.0 / n,) * 3, (n, n, n))
+    o = torch.empty((n, n, n), dtype=torch.float32, device="cuda")
+    lm.intensity(q, out=o, disorder=2, mode=1, precision=1, taylor_order=P, taylor_kernel=2)
+    torch.cuda.synchronize()
+    assert float((o.double() - got[(7, 7, 7), 0]).abs().max()) / peak < 1e-5
     rng = np.random.default_rng(21)
     G, vals = [], {0: [], 1: []}
     for H in zones:
