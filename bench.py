@@ -36,8 +36,9 @@ FP32_FMA_LANES_PER_SM, NUM_SMS = 128, 152
 # dram__bytes_read.sum + dram__bytes_write.sum of one launch of the magnetic recombination on
 # this workload, from an ncu capture of the current kernel (profiles/); None when the kernel has
 # changed since the capture
-MAG_KERNEL_TRAFFIC = 21923072
-MAG_KERNEL_TRAFFIC_SOURCE = "ncu --set full capture, profiles/k_recomb_cm_res_pyrochlore_20cubed.md"
+MAG_KERNEL = "k_recomb_rows<float,3,2,true,false>"
+MAG_KERNEL_TRAFFIC = None
+MAG_KERNEL_TRAFFIC_SOURCE = None
 
 
 def workload_config(extra=None):
@@ -398,7 +399,7 @@ def run_ours(args):
     achieved = alg_bytes / (avg_ms / 1e3) / 1e9
     hbm = float(peaks["hbm_gbs"])
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                "traffic": MAG_KERNEL_TRAFFIC, "kernel": "k_recomb_cm_res<float,3,1,4,4,false,2>",
+                "traffic": MAG_KERNEL_TRAFFIC, "kernel": MAG_KERNEL,
                 "peak_source": "%s HBM copy bandwidth (MEASURED_PEAKS.json hbm_gbs)" % peak_src,
                 "algorithmic_bytes_per_launch": alg_bytes, "avg_launch_ms": avg_ms,
                 "traffic_source": MAG_KERNEL_TRAFFIC_SOURCE,

@@ -187,6 +187,9 @@ void corner_xmax(int natom, const float *disp, const Corners &corners, double *o
 template <typename T> void recombine_cm(const RecombParams<T> &p, cudaStream_t s);
 // recomb_res.cu: the residue-class kernel when p.dres is set; false when it does not apply
 template <typename T> bool recombine_cm_residues(const RecombParams<T> &p, cudaStream_t s);
+// recomb_rows.cu: the residue-class table + whole-row writer (one form-factor class); false when it
+// does not apply
+template <typename T> bool recombine_rows(const RecombParams<T> &p, cudaStream_t s);
 template <typename T> void recombine_disp(const RecombParams<T> &p, cudaStream_t s);
 // taylor_sf.cu: the displacive recombination by sum factorisation over the zones of each k (one
 // Taylor order for the grid); false when it does not apply (zone orders, zone boxes too large)

@@ -664,6 +664,7 @@ template <typename T, int NC, int MAXS> static void launch_cm(const RecombParams
 }
 
 template <typename T> void recombine_cm(const RecombParams<T> &p, cudaStream_t s) {
+    if (recombine_rows<T>(p, s)) return;
     if (recombine_cm_residues<T>(p, s)) return;
     if (p.ncomp == 1) {
         if (p.nsite <= 4) launch_cm<T, 1, 4>(p, s);

@@ -425,7 +425,26 @@ def _special_positions_case(kind, nsite, ff, seed, cells=(5, 6, 4), shift=0):
         m.ff_coef[:, :7] = syn.J0_COEF
     elif ff == "const":
         m.ff_kind = np.zeros(nsite, dtype=np.int32)
+    elif ff == "one_g4":
+        m.ff_kind = np.full(nsite, syn.FF_GAUSS4, dtype=np.int32)
+        m.ff_coef = np.tile(syn.random_gauss4(np.random.default_rng(seed), 1), (nsite, 1))
     return m
+
+
+@pytest.mark.parametrize("prec,tag", PREC)
+@pytest.mark.parametrize("disorder,ff,mode", [(0, "one_g4", 1), (1, "one_j0", 0), (1, "one_g4", 1), (0, "const", 0)])
+def test_residue_classes_orthorhombic_cell(ctx, prec, tag, disorder, ff, mode):
+    """Special positions in an orthorhombic cell (reciprocal axes along x, y, z): the row kernel
+    factors each Gaussian of the form factor into a per-row and a per-voxel part; voxel by voxel
+    equal to the oracle, Q = 0 included, two supercells accumulated."""
+    m = _special_positions_case(disorder, 6, ff, 500 + disorder, cells=(5, 6, 4))
+    m.lattice = (4.1, 4.6, 5.2, 90.0, 90.0, 90.0)
+    G = _G(m)
+    assert np.any(np.all(G == 0, axis=1))
+    lm = to_library(ctx, m)
+    got, _ = lm.intensity(qgrid_tuple(m.qgrid), disorder=disorder, mode=mode, precision=prec)
+    fn = core.occupancy_intensity_fft if disorder == 0 else core.magnetic_intensity_fft
+    assert rel_err_of_peak(got, fn(m, G, mode)) < TOL[tag]
 
 
 @pytest.mark.parametrize("prec,tag", PREC)
