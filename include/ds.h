@@ -241,6 +241,13 @@ ds_status ds_backward(ds_model *model, const ds_qgrid *grid, const ds_opts *opts
 ds_status ds_profile_enable(ds_ctx *ctx, int enable);
 ds_status ds_profile_report(ds_ctx *ctx, char *json, size_t cap);
 
+/* Arithmetic throughput of device `device`, measured by short FMA-chain and SFU kernels (no
+ * counterpart in the paper; the denominators of the ALU rooflines reported by the benchmark).  out[5]
+ * (host): FP32 FMA TFLOP/s, FP32 paired FMA (float2) TFLOP/s, FP64 FMA TFLOP/s, SFU base-2
+ * exponentials in 10^12 per second, SFU (sin, cos) pairs in 10^12 per second.  Synchronises the
+ * device's default stream.  Errors: DS_ERR_ARG (device), DS_ERR_CUDA. */
+ds_status ds_measure_peaks(int device, double out[5]);
+
 /* Occupancy intensity for callers that cannot allocate device memory (no counterpart in the
  * paper): a host application or framework that owns all GPU memory through its own allocator,
  * a process running under a fixed memory cap, or a refinement loop that must not call the

@@ -75,6 +75,7 @@ SIGNATURES = {
     "ds_serving_pause": (st, [vp, C.c_int]),
     "ds_profile_enable": (st, [vp, C.c_int]),
     "ds_profile_report": (st, [vp, C.c_char_p, C.c_size_t]),
+    "ds_measure_peaks": (st, [C.c_int, C.POINTER(C.c_double)]),
     "ds_occupancy_intensity_noalloc": (st, [C.POINTER(C.c_double), C.c_int, vp, vp, C.c_int, C.c_int, C.c_int,
                                             C.c_int, vp, vp, C.POINTER(ds_qgrid), C.c_int, vp, vp, C.c_char_p,
                                             C.c_size_t]),

@@ -732,10 +732,11 @@ void sphere_stencil_weights(const ds_model *M, int m, int mprime, int h, std::ve
     for (double &v : w) v /= sum;
 }
 
-// smallest order whose remainder bound x_max^(P+1)/(P+1)! <= eps over the computing grid
-// (the requested grid plus the Lanczos halo); reads x_max back from the device (synchronises st)
-ds_status resolve_taylor_order(ds_model *M, const ds_qgrid *q, const ds_opts *o, cudaStream_t st, Scratch &ws, int *P,
-                               double *xmax, double *umax) {
+// queues the reduction of max |Q.u| over the atoms for the 8 corners of the computing grid (the
+// requested grid plus the Lanczos halo) and max |u|, and their copy into host_out[9] (pinned or
+// pageable host memory; valid once stream st reaches this point)
+ds_status queue_corner_xmax(ds_model *M, const ds_qgrid *q, const ds_opts *o, cudaStream_t st, Scratch &ws,
+                            double *host_out) {
     ds_ctx *ctx = M->ctx;
     int g0[3], cnt[3];
     ds_status rc = grid_indices(ctx, M, q, g0, cnt);
@@ -753,9 +754,13 @@ ds_status resolve_taylor_order(ds_model *M, const ds_qgrid *q, const ds_opts *o,
     if (ws.failed) return ds_fail(ctx, DS_ERR_OOM, "device allocation failed");
     const size_t natom = (size_t)M->nmodels * M->nsite * M->n[0] * M->n[1] * M->n[2];
     corner_xmax((int)natom, M->d_disp, corners, d_x, st);
-    double hx[9];
-    CK(cudaMemcpyAsync(hx, d_x, sizeof(hx), cudaMemcpyDeviceToHost, st));
-    CK(cudaStreamSynchronize(st));
+    CK(cudaMemcpyAsync(host_out, d_x, sizeof(double) * 9, cudaMemcpyDeviceToHost, st));
+    return DS_OK;
+}
+
+// the Taylor order of Section III C from the corner maxima hx[9] (see queue_corner_xmax)
+ds_status taylor_order_from_corners(ds_ctx *ctx, const ds_opts *o, const double hx[9], int *P, double *xmax,
+                                    double *umax) {
     double x = 0.0;
     for (int c = 0; c < 8; ++c) x = std::max(x, hx[c]);
     *xmax = x;
@@ -763,6 +768,18 @@ ds_status resolve_taylor_order(ds_model *M, const ds_qgrid *q, const ds_opts *o,
     *P = taylor_order_for(x, o->taylor_eps);
     if (*P < 0 || *P > 60) return ds_fail(ctx, DS_ERR_UNSUPPORTED, "Taylor order above 60 (x_max = %g)", x);
     return DS_OK;
+}
+
+// smallest order whose remainder bound x_max^(P+1)/(P+1)! <= eps over the computing grid
+// (the requested grid plus the Lanczos halo); reads x_max back from the device (synchronises st)
+ds_status resolve_taylor_order(ds_model *M, const ds_qgrid *q, const ds_opts *o, cudaStream_t st, Scratch &ws, int *P,
+                               double *xmax, double *umax) {
+    ds_ctx *ctx = M->ctx;
+    double hx[9];
+    ds_status rc = queue_corner_xmax(M, q, o, st, ws, hx);
+    if (rc != DS_OK) return rc;
+    CK(cudaStreamSynchronize(st));
+    return taylor_order_from_corners(ctx, o, hx, P, xmax, umax);
 }
 
 // device bytes a request takes from the pool (the caller's output excluded); P = Taylor order

@@ -90,7 +90,12 @@ struct ds_ctx {
     std::deque<ServeJob *> queue;
     std::map<uint64_t, ServeJob *> jobs;
     size_t inflight_bytes = 0;
-    std::vector<cudaStream_t> serve_streams;
+    std::vector<cudaStream_t> serve_streams;   // the first half at the highest stream priority
+    std::vector<int> stream_jobs;              // jobs in flight per serving stream
+    std::deque<double> recent_cost;            // costs of the latest admitted jobs (priority split)
+    double *plan_host = nullptr;               // pinned slots for the x_max read-backs of planning
+    std::vector<int> plan_free;                // free slots of plan_host
+    cudaStream_t plan_stream = nullptr;        // x_max reductions of served displacive requests
 };
 
 ds_status ds_fail(ds_ctx *ctx, ds_status st, const char *fmt, ...);
@@ -153,6 +158,10 @@ ds_status enqueue_request(ds_model *M, const ds_qgrid *q, const ds_opts *o, T *d
                           ds_result_info *info, const TaylorHint *hint = nullptr);
 ds_status resolve_taylor_order(ds_model *M, const ds_qgrid *q, const ds_opts *o, cudaStream_t st, Scratch &ws, int *P,
                                double *xmax, double *umax = nullptr);
+ds_status queue_corner_xmax(ds_model *M, const ds_qgrid *q, const ds_opts *o, cudaStream_t st, Scratch &ws,
+                            double *host_out);
+ds_status taylor_order_from_corners(ds_ctx *ctx, const ds_opts *o, const double hx[9], int *P, double *xmax,
+                                    double *umax);
 size_t request_footprint(const ds_model *M, const ds_qgrid *q, const ds_opts *o, int P);
 bool residue_classes(const ds_model *M, const ds::GridMap &gm, int dres[3]);
 // Lanczos resampling with the separable or the spherical cutoff (api.cu)

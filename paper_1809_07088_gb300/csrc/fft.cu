@@ -13,6 +13,7 @@
 // Large batches of small fields (whole field in shared memory) take one kernel for all three axes.
 #include <algorithm>
 
+#include "fft_reg.cuh"
 #include "internal.h"
 
 namespace ds {
@@ -261,6 +262,125 @@ __global__ void __launch_bounds__(512) k_fft_field(Geometry g, FieldSource src, 
     }
 }
 
+// Whole field in shared memory with register-resident lines (sizes N1 x N2 x N3 known at compile
+// time, every N <= 32): the field values are staged with coalesced loads as reals (rows padded to
+// N3 + 1), each thread transforms two rows along axis 3 as one complex line (rows t and t + NPAIR),
+// separates the two half spectra after a barrier (in place over the staged reals), then lines
+// along axis 2 and axis 1 are transformed in registers; the axis-1 pass writes the half spectrum
+// [k1][k2][k3 <= N3/2] straight to HBM (coalesced across the CTA), times i^n for monomials.
+// One barrier per axis.
+constexpr int FR_THREADS = 512;
+
+template <typename T, int N1, int N2, int N3>
+__global__ void __launch_bounds__(FR_THREADS, 1) k_fft_field_reg(const Geometry g, const FieldSource src, int f0,
+                                                              c_t<T> *spec) {
+    using C = c_t<T>;
+    constexpr int N3H = N3 / 2 + 1, NROW = N1 * N2, NPAIR = (NROW + 1) / 2, N3P = N3 + 1;
+    constexpr int NCELL = N1 * N2 * N3;
+    static_assert(NPAIR <= FR_THREADS, "one row pair per thread");
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C *buf = (C *)smem_raw;          // [N1][N2][N3H]
+    T *val = (T *)smem_raw;          // staged field values [row][N3P]
+    const int f = f0 + blockIdx.x, tid = threadIdx.x;
+    const FieldRow<T> fr = field_row<T>(src, NCELL, f);
+    // four consecutive cells per load (N3 % 4 == 0): 16-byte loads of the power rows, 4-byte loads
+    // of the occupancies
+    static_assert(N3 % 4 == 0, "rows of whole float4 groups");
+    for (int c4 = tid; c4 < NCELL / 4; c4 += FR_THREADS) {
+        const int c = 4 * c4, row = c / N3, r3 = c - row * N3;
+        T v[4];
+        if (fr.kind == SRC_DISP) {
+            const float4 a = ((const float4 *)fr.pw[0])[c4], b = ((const float4 *)fr.pw[1])[c4],
+                         d = ((const float4 *)fr.pw[2])[c4];
+            v[0] = a.x * b.x * d.x, v[1] = a.y * b.y * d.y, v[2] = a.z * b.z * d.z, v[3] = a.w * b.w * d.w;
+            if (fr.occ) {
+                const uchar4 o = ((const uchar4 *)fr.occ)[c4];
+                v[0] *= (T)o.x, v[1] *= (T)o.y, v[2] *= (T)o.z, v[3] *= (T)o.w;
+            }
+        } else if (fr.kind == SRC_OCC) {
+            const uchar4 o = ((const uchar4 *)fr.occ)[c4];
+            v[0] = (T)o.x - fr.mean, v[1] = (T)o.y - fr.mean, v[2] = (T)o.z - fr.mean, v[3] = (T)o.w - fr.mean;
+        } else {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) v[q] = row_value<T>(fr, c + q);
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) val[row * N3P + r3 + q] = v[q];
+    }
+    __syncthreads();
+    // axis 3: rows t and t + NPAIR as the real and imaginary parts of one line
+    C z[N3];
+    const bool has1 = tid + NPAIR < NROW;
+    if (tid < NPAIR) {
+#pragma unroll
+        for (int r3 = 0; r3 < N3; ++r3)
+            z[r3] = mk<T>(val[tid * N3P + r3], has1 ? val[(tid + NPAIR) * N3P + r3] : T(0));
+        RegFFT<T, N3>::run(z);
+    }
+    __syncthreads();
+    if (tid < NPAIR) {
+        // X = (Z_k + conj Z_{-k}) / 2 (row t), Y = (Z_k - conj Z_{-k}) / (2i) (row t + NPAIR)
+#pragma unroll
+        for (int k = 0; k < N3H; ++k) {
+            const C zk = z[k], zm = z[(N3 - k) % N3];
+            buf[tid * N3H + k] = mk<T>(T(0.5) * (zk.x + zm.x), T(0.5) * (zk.y - zm.y));
+            if (has1) buf[(tid + NPAIR) * N3H + k] = mk<T>(T(0.5) * (zk.y + zm.y), T(-0.5) * (zk.x - zm.x));
+        }
+    }
+    __syncthreads();
+    // axis 2: line (R1, k3), elements R2 N3H apart
+    for (int L = tid; L < N1 * N3H; L += FR_THREADS) {
+        const int r1 = L / N3H, k3 = L - r1 * N3H;
+        C *line = buf + r1 * N2 * N3H + k3;
+        C y[N2];
+#pragma unroll
+        for (int i = 0; i < N2; ++i) y[i] = line[i * N3H];
+        RegFFT<T, N2>::run(y);
+#pragma unroll
+        for (int i = 0; i < N2; ++i) line[i * N3H] = y[i];
+    }
+    __syncthreads();
+    // axis 1: line (k2, k3), elements R1 N2 N3H apart; half spectrum to HBM
+    int rot = 0;
+    if (src.kind == SRC_DISP) rot = src.terms[(f % src.nf_per_model) % src.T].w;
+    C *out = spec + (size_t)f * (N1 * N2 * N3H);
+    for (int L = tid; L < N2 * N3H; L += FR_THREADS) {
+        C y[N1];
+#pragma unroll
+        for (int i = 0; i < N1; ++i) y[i] = buf[i * N2 * N3H + L];
+        RegFFT<T, N1>::run(y);
+#pragma unroll
+        for (int i = 0; i < N1; ++i) out[i * N2 * N3H + L] = cipow(y[i], rot);
+    }
+}
+
+template <typename T, int N> static bool launch_field_reg(const Geometry &g, const FieldSource &src, int f0, int nf,
+                                                          c_t<T> *spec, cudaStream_t s) {
+    constexpr size_t sm = (size_t)N * N * (N / 2 + 1) * sizeof(c_t<T>);
+    if (sm > 48 * 1024)
+        cudaFuncSetAttribute(k_fft_field_reg<T, N, N, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_fft_field_reg<T, N, N, N><<<(unsigned)nf, FR_THREADS, sm, s>>>(g, src, f0, spec);
+    count_launches(1);
+    return true;
+}
+
+// the register kernel for cubic FP32 supercells of 8, 16, 20 or 32 cells per axis
+template <typename T>
+static bool fft_field_reg(const Geometry &g, const FieldSource &src, int f0, int nf, c_t<T> *spec, cudaStream_t s) {
+    if constexpr (sizeof(T) != 4) {
+        return false;
+    } else {
+        if (g.n[0] != g.n[1] || g.n[1] != g.n[2]) return false;
+        switch (g.n[0]) {
+            case 8: return launch_field_reg<T, 8>(g, src, f0, nf, spec, s);
+            case 16: return launch_field_reg<T, 16>(g, src, f0, nf, spec, s);
+            case 20: return launch_field_reg<T, 20>(g, src, f0, nf, spec, s);
+            case 32: return launch_field_reg<T, 32>(g, src, f0, nf, spec, s);
+            default: return false;
+        }
+    }
+}
+
 // shared memory of the whole-field kernel (0 when a field does not fit)
 static size_t field_smem(const Geometry &g, size_t ce) {
     const int n2p = (g.n[1] + 1) / 2;
@@ -313,6 +433,7 @@ static void fft_two_pass(const Geometry &g, const FieldSource &src, int f0, int 
 template <typename T>
 void fft_real_fields(const Geometry &g, const FieldSource &src, int f0, int nf, c_t<T> *work, c_t<T> *spec,
                      const c_t<T> *W1, const c_t<T> *W2, const c_t<T> *W3, cudaStream_t s) {
+    if (fft_field_reg<T>(g, src, f0, nf, spec, s)) return;
     // whole-field kernel: for batches large enough to fill the GPU with one CTA per field, on
     // supercells of at least 18^3 cells (measured on GB300: 1.4x faster than the two passes at
     // 20^3 x 1024 fields, even at 16^3 x 2000, slower for 8^3 or for fewer fields)

@@ -135,6 +135,28 @@ def test_fft_sizes_all_radices(ctx, cells):
     assert rel_err_of_peak(got, want) < TOL["fp64"]
 
 
+@pytest.mark.parametrize("n", [8, 16, 20, 32])
+@pytest.mark.parametrize("kind", [0, 1, 2])
+def test_fft_register_kernel_cubic_sizes(ctx, n, kind):
+    """Cubic FP32 supercells of 8, 16, 20 and 32 cells (one CTA per field, lines in registers):
+    occupancy, moments and Taylor monomials (the i^n factor of every order), two supercells, against
+    the oracle's FFT method."""
+    q = syn.QGrid(h0=(-1.0 - 2.0 / n,) * 3, step=(1.0 / n,) * 3, count=(n + 5, n + 3, 2 * n + 1))
+    m = syn.small_case(kind, cells=(n, n, n), nsite=2, nmodels=2, seed=600 + n + kind, qgrid=q)
+    lm = to_library(ctx, m)
+    G = _G(m)
+    if kind == 2:
+        got, _ = lm.intensity(qgrid_tuple(q), disorder=2, mode=1, precision=1, taylor_order=5)
+        want = core.displacive_intensity_fft(m, G, 1, P=5)
+    elif kind == 1:
+        got, _ = lm.intensity(qgrid_tuple(q), disorder=1, mode=0, precision=1)
+        want = core.magnetic_intensity_fft(m, G, 0)
+    else:
+        got, _ = lm.intensity(qgrid_tuple(q), disorder=0, mode=1, precision=1)
+        want = core.occupancy_intensity_fft(m, G, 1)
+    assert rel_err_of_peak(got, want) < TOL["fp32"]
+
+
 @pytest.mark.parametrize("prec,tag", PREC)
 def test_fft_two_pass_radices(ctx, prec, tag):
     """A supercell too large for the whole-field FFT kernel (30 x 28 x 35: radices 2, 3, 4, 5, 7)

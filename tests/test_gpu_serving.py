@@ -124,3 +124,30 @@ def test_served_and_direct_displacive_requests_on_one_model_concurrently():
     for P in direct_P:
         assert np.array_equal(direct[P], alone[P]), P
     ctx.close()
+
+
+def test_served_fp32_results_match_the_plain_fp64_path():
+    """A mixed stream (occupancy, moments, displacive with automatic orders planned on the GPU,
+    Lanczos) served in FP32 on concurrent streams: every result within 1e-5 of peak of the same
+    request computed alone on the plain FP64 path, and the displacive ones with the FP64 path's
+    Taylor order."""
+    import torch
+    import paper_1809_07088_gb300 as ds
+    ctx = ds.Context(0)
+    reqs = _requests()
+    models = [to_library(ctx, m) for m, _ in reqs]
+    outs, tickets = [], []
+    for lm, (m, o) in zip(models, reqs):
+        o32 = dict(o, precision=1)
+        out = torch.full(m.qgrid.count, float("nan"), dtype=torch.float32, device="cuda")
+        outs.append(out)
+        tickets.append(lm.submit(qgrid_tuple(m.qgrid), out, **o32))
+    infos = [ctx.wait(t, 120.0) for t in tickets]
+    for lm, out, info, (m, o) in zip(models, outs, infos, reqs):
+        want, info64 = lm.intensity(qgrid_tuple(m.qgrid), **dict(o, precision=0))
+        got = out.cpu().numpy()
+        assert np.isfinite(got).all()
+        assert np.max(np.abs(got - want)) <= 1e-5 * np.max(np.abs(want))
+        if o["disorder"] == 2:
+            assert info.taylor_order == info64["taylor_order"] and info.x_max == info64["x_max"]
+    ctx.close()
