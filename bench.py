@@ -548,6 +548,27 @@ def taylor_sf_flops(cells, qgrid, P, nsite):
     return 4.0 * work * nsite
 
 
+def taylor_sf_adjoint_flops(cells, qgrid, P, nsite):
+    """Multiply-adds of the transposed sum factorisation of the adjoint: per k of the full grid and
+    per site, (P+1) n1 n2 n3 + (P+1)(P+2)/2 n2 n3 + T(P) n3 over the k's box of zones, 4 flop each."""
+    import numpy as np
+    n = list(cells)
+    g0 = [int(round(qgrid.h0[a] * n[a])) for a in range(3)]
+    cnt = list(qgrid.count)
+    T = (P + 1) * (P + 2) * (P + 3) / 6.0
+    nab = (P + 1) * (P + 2) / 2.0
+    nz = []
+    for a in range(3):
+        k = np.arange(n[a])
+        lo = -((-(g0[a] - k)) // n[a])
+        hi = (g0[a] + cnt[a] - 1 - k) // n[a]
+        nz.append(np.maximum(hi - lo + 1, 0).astype(np.float64))
+    n1, n2, n3 = nz
+    s1, s2, s3 = n1.sum(), n2.sum(), n3.sum()
+    work = (P + 1) * s1 * s2 * s3 + nab * n1.size * s2 * s3 + T * n1.size * n2.size * s3
+    return 4.0 * work * nsite
+
+
 def fft_side_comparison(dev, nfields, cells, ours_ms, reps=3):
     """Timed side comparison, not on the path: cuFFT (through torch.fft.rfftn) on the same batch
     of real fields, materialised in HBM (the library generates the monomials inside its first
@@ -640,7 +661,14 @@ def run_rows(dev, cpu_rows=True):
     g = torch.empty((1, m.nsite) + tuple(m.cells) + (3,), dtype=torch.float32, device=dev)
     ms, st = timed(lambda: lm.backward(q, dL, grad=g, disorder=ds.DS_DISP, mode=ds.DS_TOTAL, precision=ds.DS_FP32,
                                        taylor_order=-1, taylor_eps=1e-8), reps=2)
-    rows["adjoint_fcc32"] = {"workload": "dchi2/du of the fcc 32^3 case above, FP32", "ms": ms, "stages_ms": st}
+    az = st.get("adjoint_z", float("nan"))
+    aflops = taylor_sf_adjoint_flops(m.cells, m.qgrid, rows["taylor_fcc32_zonal0"]["taylor_order"], m.nsite)
+    rows["adjoint_fcc32"] = {"workload": "dchi2/du of the fcc 32^3 case above, FP32", "ms": ms, "stages_ms": st,
+                             "kernel": "k_adj_taylor_sf (transposed sum factorisation)",
+                             "roofline": {"bound": "alu", "achieved": aflops / (az / 1e3) / 1e12, "peak": fp32,
+                                          "unit": "TFLOP/s", "frac": aflops / (az / 1e3) / 1e12 / fp32,
+                                          "note": "multiply-adds of the three power sums over each k's zones "
+                                                  "(complex x real = 4 flop), peak measured in this run"}}
     # side comparison only (not on the path): the library FFT of the same batch of fields
     nf_fcc = m.nsite * rows["taylor_fcc32_zonal0"]["monomials"]
     rows["fft_side_comparison"] = fft_side_comparison(dev, nf_fcc, m.cells,

@@ -27,6 +27,13 @@
 
 using namespace ds;
 
+namespace ds {
+// adjoint_sf.cu: Z of the displacive adjoint by the transposed sum factorisation (FP32); false when
+// it does not apply (order above 31, zone boxes wider than 17)
+bool adjoint_z_disp_sf(const RecombParams<float> &p, const float *dLdI, const float2 *F, int P, double scale,
+                       float2 *Z, cudaStream_t s);
+}  // namespace ds
+
 namespace {
 
 __device__ __forceinline__ int fdiv(int a, int b) {
@@ -374,7 +381,13 @@ ds_status backward_run(ds_model *M, const ds_qgrid *q, const ds_opts *o, const T
         ProfScope ps(ctx, "adjoint_z", st);
         for (int m = 0; m < nmod; ++m) {
             p.model = m;
-            if (mag) {
+            bool done = false;
+            if constexpr (sizeof(T) == 4) {
+                // FP32: the transposed sum factorisation over each k's zones (adjoint_sf.cu)
+                if (!mag) done = adjoint_z_disp_sf(p, dLdI, F, keep.src.P, 2.0 / (nmod * N), Z, st);
+            }
+            if (done) {
+            } else if (mag) {
                 k_adj_z_mag<T><<<g.ncell, 3 * nsite, 0, st>>>(p, dLdI, F, 2.0 * 0.07265 / (nmod * N), Z);
             } else {
                 constexpr int TPT = sizeof(T) == 4 ? 4 : 2;
@@ -396,7 +409,7 @@ ds_status backward_run(ds_model *M, const ds_qgrid *q, const ds_opts *o, const T
                     default: launch(k_adj_z_disp<T, 16, 1>, 1); break;
                 }
             }
-            count_launches(1);
+            if (!done) count_launches(1);
         }
     }
     {
