@@ -12,7 +12,9 @@
 // with the powers of each axis tabulated once per k.  Each thread owns one output row of a step and
 // four consecutive powers (registers); every sum runs over the zones of one axis in a fixed order.
 //
-// CTA: one k of the full grid (the adjoint's complex FFT takes every k), 512 threads; per site the
+// CTA: one k of the full grid (the adjoint's complex FFT takes every k), shared memory sized for the
+// widest zone box of the grid (zr zones per axis), 128, 256 or 512 threads as that footprint lets
+// 16 warps reside on an SM; per site the
 // zone factors beta are formed from gamma = scale dL/dI conj(F) (shared memory, once per k) and the
 // site's phases and form factor.
 #include <algorithm>
@@ -24,12 +26,11 @@ namespace ds {
 
 namespace {
 
-constexpr int AS_THREADS = 512;
-constexpr int AS_ZR = 17;        // zones per axis handled
+constexpr int AS_ZR = 17;        // zones per axis handled (at most)
 constexpr int AS_PMAX = 31;      // Taylor order handled
 constexpr int AS_CH = 4;         // powers per thread item
 
-__device__ __forceinline__ int fdivf(int a, int b) {
+__host__ __device__ __forceinline__ int fdivf(int a, int b) {
     int q = a / b;
     if ((a % b != 0) && ((a < 0) != (b < 0))) --q;
     return q;
@@ -38,22 +39,23 @@ __device__ __forceinline__ int fdivf(int a, int b) {
 struct AdjLayout {
     size_t gam, bv, W, pw, total;
 };
-__host__ __device__ __forceinline__ AdjLayout adj_layout(int P) {
+__host__ __device__ __forceinline__ AdjLayout adj_layout(int P, int zr) {
     auto al = [](size_t x) { return (x + 15) & ~(size_t)15; };
-    const size_t z3 = (size_t)AS_ZR * AS_ZR * AS_ZR, nab = (size_t)(P + 1) * (P + 2) / 2;
+    const size_t z3 = (size_t)zr * zr * zr, nab = (size_t)(P + 1) * (P + 2) / 2;
     AdjLayout L;
     L.gam = 0;
     L.bv = al(L.gam + z3 * sizeof(float2));
-    L.W = al(L.bv + std::max(z3, nab * AS_ZR) * sizeof(float2));
-    L.pw = al(L.W + (size_t)(P + 1) * AS_ZR * AS_ZR * sizeof(float2));
-    L.total = al(L.pw + (size_t)3 * AS_ZR * (P + 1) * sizeof(float));
+    L.W = al(L.bv + std::max(z3, nab * zr) * sizeof(float2));
+    L.pw = al(L.W + (size_t)(P + 1) * zr * zr * sizeof(float2));
+    L.total = al(L.pw + (size_t)3 * zr * (P + 1) * sizeof(float));
     return L;
 }
 
 }  // namespace
 
-__global__ void __launch_bounds__(AS_THREADS, 1)
-    k_adj_taylor_sf(const __grid_constant__ RecombParams<float> p, const float *dLdI, const float2 *F, int P,
+template <int AS_THREADS>
+__global__ void __launch_bounds__(AS_THREADS, 512 / AS_THREADS)
+    k_adj_taylor_sf(const __grid_constant__ RecombParams<float> p, const float *dLdI, const float2 *F, int P, int zr,
                     float scale, float2 *Z) {
     extern __shared__ __align__(16) unsigned char smem[];
     const Geometry &g = p.g;
@@ -80,15 +82,15 @@ __global__ void __launch_bounds__(AS_THREADS, 1)
         return;
     }
     const int nz1 = nz[0], nz2 = nz[1], nz3 = nz[2], ncol = nz2 * nz3, nzone = nz1 * ncol;
-    const AdjLayout L = adj_layout(P);
+    const AdjLayout L = adj_layout(P, zr);
     float2 *gam = (float2 *)(smem + L.gam);   // [h1][h2][h3]
     float2 *bv = (float2 *)(smem + L.bv);     // beta [h1][col], then V [(a, b)][h3]
     float2 *W = (float2 *)(smem + L.W);       // [a][col]
     float *pw = (float *)(smem + L.pw);       // [axis][zone][e]
 
     // powers x_a(j)^e of the scaled coefficient variables
-    for (int i = tid; i < 3 * AS_ZR; i += AS_THREADS) {
-        const int a = i / AS_ZR, j = i - a * AS_ZR;
+    for (int i = tid; i < 3 * zr; i += AS_THREADS) {
+        const int a = i / zr, j = i - a * zr;
         const double x = ((double)(lo[a] + j) + (double)kk[a] / g.n[a]) / p.gscale[a];
         double v = 1.0;
         for (int e = 0; e <= P; ++e) {
@@ -143,7 +145,7 @@ __global__ void __launch_bounds__(AS_THREADS, 1)
             for (int q = 0; q < AS_CH; ++q) acc[q] = make_float2(0.f, 0.f);
             for (int h1 = 0; h1 < nz1; ++h1) {
                 const float2 b = bv[h1 * ncol + col];
-                const float *pp = pw + (size_t)(0 * AS_ZR + h1) * P1 + a0;
+                const float *pp = pw + (size_t)(0 * zr + h1) * P1 + a0;
 #pragma unroll
                 for (int q = 0; q < AS_CH; ++q)
                     if (a0 + q < P1) acc[q] = __ffma2_rn(make_float2(pp[q], pp[q]), b, acc[q]);
@@ -162,7 +164,7 @@ __global__ void __launch_bounds__(AS_THREADS, 1)
             for (int q = 0; q < AS_CH; ++q) acc[q] = make_float2(0.f, 0.f);
             for (int h2 = 0; h2 < nz2; ++h2) {
                 const float2 w = W[(size_t)a * ncol + h2 * nz3 + h3];
-                const float *pp = pw + (size_t)(1 * AS_ZR + h2) * P1 + b0;
+                const float *pp = pw + (size_t)(1 * zr + h2) * P1 + b0;
 #pragma unroll
                 for (int q = 0; q < AS_CH; ++q)
                     if (b0 + q <= P - a) acc[q] = __ffma2_rn(make_float2(pp[q], pp[q]), w, acc[q]);
@@ -188,7 +190,7 @@ __global__ void __launch_bounds__(AS_THREADS, 1)
             for (int q = 0; q < AS_CH; ++q) acc[q] = make_float2(0.f, 0.f);
             for (int h3 = 0; h3 < nz3; ++h3) {
                 const float2 v = bv[(size_t)ab * nz3 + h3];
-                const float *pp = pw + (size_t)(2 * AS_ZR + h3) * P1 + c0;
+                const float *pp = pw + (size_t)(2 * zr + h3) * P1 + c0;
 #pragma unroll
                 for (int q = 0; q < AS_CH; ++q)
                     if (c0 + q <= lc) acc[q] = __ffma2_rn(make_float2(pp[q], pp[q]), v, acc[q]);
@@ -208,12 +210,32 @@ __global__ void __launch_bounds__(AS_THREADS, 1)
 bool adjoint_z_disp_sf(const RecombParams<float> &p, const float *dLdI, const float2 *F, int P, double scale,
                        float2 *Z, cudaStream_t s) {
     if (P > AS_PMAX) return false;
+    // widest zone box of any k along any axis
+    int zr = 1;
     for (int a = 0; a < 3; ++a)
-        if ((p.gm.cnt[a] + p.g.n[a] - 1) / p.g.n[a] + 1 > AS_ZR) return false;
-    const AdjLayout L = adj_layout(P);
+        for (int k = 0; k < p.g.n[a]; ++k) {
+            const int lo = -fdivf(-(p.gm.g0[a] - k), p.g.n[a]);
+            const int hi = fdivf(p.gm.g0[a] + p.gm.cnt[a] - 1 - k, p.g.n[a]);
+            zr = std::max(zr, hi - lo + 1);
+        }
+    if (zr > AS_ZR) return false;
+    const AdjLayout L = adj_layout(P, zr);
     if (L.total > 227 * 1024) return false;
-    cudaFuncSetAttribute(k_adj_taylor_sf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total);
-    k_adj_taylor_sf<<<(unsigned)p.g.ncell, AS_THREADS, L.total, s>>>(p, dLdI, F, P, (float)scale, Z);
+    const unsigned nb = (unsigned)p.g.ncell;
+    switch (sf_threads_for(L.total)) {
+        case 128:
+            cudaFuncSetAttribute(k_adj_taylor_sf<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total);
+            k_adj_taylor_sf<128><<<nb, 128, L.total, s>>>(p, dLdI, F, P, zr, (float)scale, Z);
+            break;
+        case 256:
+            cudaFuncSetAttribute(k_adj_taylor_sf<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total);
+            k_adj_taylor_sf<256><<<nb, 256, L.total, s>>>(p, dLdI, F, P, zr, (float)scale, Z);
+            break;
+        default:
+            cudaFuncSetAttribute(k_adj_taylor_sf<512>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total);
+            k_adj_taylor_sf<512><<<nb, 512, L.total, s>>>(p, dLdI, F, P, zr, (float)scale, Z);
+            break;
+    }
     count_launches(1);
     return true;
 }

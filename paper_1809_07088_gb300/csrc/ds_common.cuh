@@ -95,6 +95,16 @@ __device__ __forceinline__ float exp2_w(float x) {
     return y;
 }
 // 1/x: the SFU's approximate reciprocal (PTX rcp.approx) in FP32, exact division in FP64
+// asynchronous global -> shared copies of BYTES (4, 8 or 16) bytes, in commit groups
+template <int BYTES> __device__ __forceinline__ void cp_async(void *smem, const void *gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(s), "l"(gmem), "n"(BYTES) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+// wait until at most N of this thread's most recent groups are still in flight
+template <int N> __device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
 __device__ __forceinline__ double rcp_w(double x) { return 1.0 / x; }
 __device__ __forceinline__ float rcp_w(float x) {
     float y;

@@ -112,6 +112,7 @@ struct SFPlan {
     int xpad;                          // row stride of the per-group partial sums X[h3][item]
     int ymax;                          // largest group (a values)
     size_t smem;                       // dynamic shared memory of one CTA
+    int nthr;                          // threads per CTA (128, 256 or 512: 16 warps per SM)
     const int4 *items;                 // slots: (a, b, t0, xi), a < 0 = empty slot
 };
 
@@ -197,6 +198,8 @@ template <typename T> void recombine_disp_sf(const RecombParams<T> &p, cudaStrea
 // host plan of that kernel (false: zone boxes wider than it handles, or, unless forced, more work
 // than the per-voxel recombination); `items` is the slot table to upload, its device address then
 // goes into plan.items
+// threads per CTA (128, 256 or 512) keeping 16 warps on an SM for a dynamic shared-memory footprint
+int sf_threads_for(size_t smem);
 bool taylor_sf_plan(const Geometry &g, const GridMap &gm, int P, int nsite, size_t celem, bool force, SFPlan &plan,
                     std::vector<int4> &items);
 template <typename T>

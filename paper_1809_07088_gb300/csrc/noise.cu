@@ -8,8 +8,10 @@
 // intensity_convol_finite both cancel in the normalisation).  r_cut = (1 - 1/m)/m' and
 // m_eff = m m' / 2 (m' = 2 is the plain window; larger m' reaches zero at 1/m').  Each pass
 // shrinks the volume by the halo h = ceil(m_eff) - 1 on both sides of its axis.  Stencils of up
-// to 17 taps run as sliding windows (each input read about once per pass: HBM bound); wider
-// ones with one thread per output.
+// to 17 taps run as two streaming passes: the two in-plane axes fused (one read of the
+// halo-extended volume, one write of the intermediate), then the strided outer axis as a sliding
+// window (one read, one write): HBM bound, about 16 bytes per FP32 voxel.  Wider stencils take one
+// thread per output and one pass per axis.
 #include <algorithm>
 
 #include "internal.h"
@@ -90,7 +92,9 @@ template <typename T> struct Taps {
 // Pass along the middle axis of a volume viewed as [A][B][C] (C contiguous): out[a][b][c] =
 // sum_t w_t in[a][b + t][c], b < B - 2h.  A thread owns one (a, c) column and a run of L
 // outputs along B, keeping the last NT inputs in registers (a sliding window), so each input is
-// read about (L + NT - 1) / L times; consecutive threads take consecutive c (coalesced).
+// read about (L + NT - 1) / L times; consecutive threads take consecutive c (coalesced).  The
+// inputs of LM_U outputs are loaded together, so that many loads are in flight per thread.
+constexpr int LM_U = 8;
 template <typename T, int NT>
 __global__ void __launch_bounds__(256) k_lanczos_mid(const T *__restrict__ in, T *__restrict__ out, int A, int B, int C,
                                                      int L, const __grid_constant__ Taps<T> tp) {
@@ -105,39 +109,82 @@ __global__ void __launch_bounds__(256) k_lanczos_mid(const T *__restrict__ in, T
     T ring[NT];
 #pragma unroll
     for (int t = 0; t < NT - 1; ++t) ring[t] = src[(size_t)t * C];
-    for (int b = b0; b < b1; ++b) {
-        ring[NT - 1] = src[(size_t)(b - b0 + NT - 1) * C];
-        T acc = T(0);
+    for (int b = b0; b < b1; b += LM_U) {
+        T nx[LM_U];
 #pragma unroll
-        for (int t = 0; t < NT; ++t) acc = fma(tp.w[t], ring[t], acc);
-        dst[(size_t)(b - b0) * C] = acc;
+        for (int u = 0; u < LM_U; ++u) nx[u] = b + u < b1 ? src[(size_t)(b - b0 + u + NT - 1) * C] : T(0);
 #pragma unroll
-        for (int t = 0; t < NT - 1; ++t) ring[t] = ring[t + 1];
+        for (int u = 0; u < LM_U; ++u) {
+            ring[NT - 1] = nx[u];
+            T acc = T(0);
+#pragma unroll
+            for (int t = 0; t < NT; ++t) acc = fma(tp.w[t], ring[t], acc);
+            if (b + u < b1) dst[(size_t)(b - b0 + u) * C] = acc;
+#pragma unroll
+            for (int t = 0; t < NT - 1; ++t) ring[t] = ring[t + 1];
+        }
     }
 }
 
-// Pass along the contiguous axis of [R][C]: a block stages a row segment and its halo in shared
-// memory (coalesced), then each thread forms outputs from the staged values.
+// Fused in-plane pass over [A][B][C] (C contiguous): out[a][b][c] = sum_s w_s sum_t w_t
+// in[a][b + s][c + t] for b < B - 2h, c < C - 2h.  A CTA owns a segment of 256 outputs along C and
+// a run of L outputs along B of one a; it streams the run's L + NT - 1 input rows through a ring
+// of LP_D row buffers in shared memory, filled by asynchronous copies LP_D - 1 rows ahead (one
+// barrier per row).  Every thread forms the axis-C stencil of a staged row at its column and
+// keeps the last NT such values in registers, from which the axis-B stencil gives one output row
+// per input row.
+constexpr int LP_D = 8;
 template <typename T, int NT>
-__global__ void __launch_bounds__(256) k_lanczos_row(const T *__restrict__ in, T *__restrict__ out, int C, int SEG,
-                                                     const __grid_constant__ Taps<T> tp) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    T *seg = (T *)smem_raw;
-    const int Co = C - (NT - 1);
-    const int nseg = (Co + SEG - 1) / SEG;
-    const size_t r = blockIdx.x / nseg;
-    const int s0 = (int)(blockIdx.x - r * nseg) * SEG;
-    const int n = min(SEG, Co - s0);
-    const T *src = in + r * C + s0;
-    for (int i = threadIdx.x; i < n + NT - 1; i += blockDim.x) seg[i] = src[i];
-    __syncthreads();
-    T *dst = out + r * Co + s0;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
-        T acc = T(0);
+__global__ void __launch_bounds__(256) k_lanczos_plane(const T *__restrict__ in, T *__restrict__ out, int A, int B,
+                                                       int C, int L, const __grid_constant__ Taps<T> tp) {
+    constexpr int TC = 256, W = TC + NT - 1;
+    __shared__ __align__(16) T buf[LP_D][W];
+    const int tid = threadIdx.x;
+    const int Bo = B - (NT - 1), Co = C - (NT - 1);
+    const int nrun = (Bo + L - 1) / L;
+    const int a = blockIdx.y / nrun, run = blockIdx.y - a * nrun;
+    const int c0 = blockIdx.x * TC;
+    const int b0 = run * L, b1 = min(Bo, b0 + L);
+    const int nw = min(W, C - c0);          // staged inputs of a row segment
+    const T *src = in + ((size_t)a * B + b0) * C + c0;
+    T *dst = out + ((size_t)a * Bo + b0) * Co + c0 + tid;
+    const bool act = c0 + tid < Co;
+    const int nrow = b1 - b0 + NT - 1;
+    // row i of the run into buffer i mod LP_D (one commit group per row, empty past the run)
+    auto issue = [&](int i) {
+        if (i < nrow) {
+            const T *row = src + (size_t)i * C;
+            T *sb = buf[i % LP_D];
+            for (int j = tid; j < nw; j += TC) cp_async<sizeof(T)>(sb + j, row + j);
+        }
+        cp_async_commit();
+    };
 #pragma unroll
-        for (int t = 0; t < NT; ++t) acc = fma(tp.w[t], seg[i + t], acc);
-        dst[i] = acc;
+    for (int i = 0; i < LP_D - 1; ++i) issue(i);
+    T ring[NT];
+#pragma unroll
+    for (int t = 0; t < NT; ++t) ring[t] = T(0);
+    for (int i = 0; i < nrow; ++i) {
+        cp_async_wait<LP_D - 2>();   // row i has landed (this thread's copies)
+        __syncthreads();             // every thread's copies of row i; row i - 1 is no longer read
+        issue(i + LP_D - 1);         // into the buffer row i - 1 used
+        const T *sb = buf[i % LP_D];
+        T x = T(0);
+        if (act) {
+#pragma unroll
+            for (int t = 0; t < NT; ++t) x = fma(tp.w[t], sb[tid + t], x);
+        }
+#pragma unroll
+        for (int t = 0; t < NT - 1; ++t) ring[t] = ring[t + 1];
+        ring[NT - 1] = x;
+        if (i >= NT - 1 && act) {
+            T acc = T(0);
+#pragma unroll
+            for (int t = 0; t < NT; ++t) acc = fma(tp.w[t], ring[t], acc);
+            dst[(size_t)(i - (NT - 1)) * Co] = acc;
+        }
     }
+    cp_async_wait<0>();
 }
 
 template <typename T, int NT>
@@ -145,28 +192,38 @@ static void sliding_passes(const T *ext, T *tmp1, T *tmp2, T *out, int d[3], con
     Taps<T> tp;
     for (int i = 0; i < 64; ++i) tp.w[i] = i < NT ? (T)wd[i] : T(0);
     const int h = (NT - 1) / 2;
-    // axis 2 (contiguous): rows of d2, segments of up to 2048 outputs
+    // runs of L outputs along the streamed axis: long enough that the NT - 1 halo rows re-read per
+    // run stay a small fraction, short enough that the grid still fills the SMs several times
+    auto run_len = [&](long long cols, int A, int Bo) {
+        int L = 256;
+        while (L > 32 && cols * A * (long long)((Bo + L - 1) / L) < 152LL * 8 * 4) L /= 2;
+        // A x runs on the grid's y axis (at most 65535)
+        const int maxrun = std::max(1, 65535 / A);
+        return std::max(L, (Bo + maxrun - 1) / maxrun);
+    };
+    // axes 2 and 1 fused: [d0][d1][d2] -> [d0][d1 - 2h][d2 - 2h]
     {
-        const size_t R = (size_t)d[0] * d[1];
-        const int Co = d[2] - 2 * h, SEG = std::min(Co, 2048);
-        const size_t nb = R * (size_t)((Co + SEG - 1) / SEG);
-        k_lanczos_row<T, NT><<<(unsigned)nb, 256, (SEG + NT - 1) * sizeof(T), s>>>(ext, tmp1, d[2], SEG, tp);
+        const int Bo = d[1] - 2 * h, Co = d[2] - 2 * h;
+        const long long nseg = (Co + 255) / 256;
+        const int L = run_len(nseg, d[0], Bo);
+        const int nrun = (Bo + L - 1) / L;
+        dim3 grid((unsigned)nseg, (unsigned)(d[0] * nrun));
+        k_lanczos_plane<T, NT><<<grid, 256, 0, s>>>(ext, tmp1, d[0], d[1], d[2], L, tp);
+        d[1] = Bo;
         d[2] = Co;
     }
-    // axis 1: [d0][d1][d2], then axis 0: [1][d0][d1 d2]; runs of L outputs per thread
-    auto mid = [&](const T *a, T *b, int A, int B, int C) {
-        // runs of at least 64 outputs, longer when A x runs would exceed the grid's y limit
-        const int Bo = B - 2 * h;
-        const int L = std::max(64, (int)(((long long)Bo * A + 65534) / 65535));
+    // axis 0 as the middle axis of [1][d0][d1 d2]
+    {
+        const int C = d[1] * d[2], Bo = d[0] - 2 * h;
+        const long long nseg = (C + 255) / 256;
+        const int L = run_len(nseg, 1, Bo);
         const int nrun = (Bo + L - 1) / L;
-        dim3 grid((unsigned)((C + 255) / 256), (unsigned)(A * nrun));
-        k_lanczos_mid<T, NT><<<grid, 256, 0, s>>>(a, b, A, B, C, L, tp);
-    };
-    mid(tmp1, tmp2, d[0], d[1], d[2]);
-    d[1] -= 2 * h;
-    mid(tmp2, out, 1, d[0], d[1] * d[2]);
-    d[0] -= 2 * h;
-    count_launches(3);
+        dim3 grid((unsigned)nseg, (unsigned)nrun);
+        k_lanczos_mid<T, NT><<<grid, 256, 0, s>>>(tmp1, out, 1, d[0], C, L, tp);
+        d[0] = Bo;
+    }
+    (void)tmp2;
+    count_launches(2);
 }
 
 template <typename T>

@@ -695,15 +695,6 @@ constexpr int DISP_KT = 8;
 constexpr int DISP_TC = 32;
 enum { OP_MULZ = 0, OP_NEWB = 1, OP_NEWA = 2, OP_INIT = 3 };
 
-template <int BYTES> __device__ __forceinline__ void cp_async(void *smem, const void *gmem) {
-    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(s), "l"(gmem), "n"(BYTES) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int N> __device__ __forceinline__ void cp_async_wait() {
-    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
-}
-
 struct ZoneBox {
     int lo[3], n[3];
 };

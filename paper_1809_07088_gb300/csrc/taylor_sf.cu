@@ -21,7 +21,8 @@
 // the voxel -G with conj(F)).  When both boxes coincide (a grid symmetric about 0) one evaluation
 // serves both.
 //
-// CTA: one stored k and one box (blockIdx.y = 0 direct, 1 mirror), 512 threads.  Per site: the
+// CTA: one stored k and one box (blockIdx.y = 0 direct, 1 mirror), 128, 256 or 512 threads, as
+// many as keep 16 warps on an SM with the CTAs its shared memory admits.  Per site: the
 // (a, b) chains of step 1 are spread over the threads in a balanced slot order (host table) and
 // read M'(k) straight from the spectra; X and Y live in shared memory; step 3 threads own one
 // (h2, h3) column each and add phi_mu(G) S into F (shared memory).  Exponents a are processed in
@@ -38,7 +39,6 @@ namespace ds {
 
 namespace {
 
-constexpr int SF_THREADS = 512;
 constexpr size_t SF_SMEM_MAX = 227 * 1024;
 
 __device__ __forceinline__ int fdiv_floor(int a, int b) {
@@ -117,8 +117,8 @@ __host__ __device__ __forceinline__ SFLayout sf_layout(int zr, int nsite, int xp
 
 // One CTA: stored k = blockIdx.x, box blockIdx.y (0 direct, 1 mirror).  ZR: zones per axis held in
 // registers by the Horner recurrences (>= the box extents).
-template <typename T, int ZR>
-__global__ void __launch_bounds__(SF_THREADS, 1) k_taylor_sf(const __grid_constant__ RecombParams<T> p) {
+template <typename T, int ZR, int NT>
+__global__ void __launch_bounds__(NT, 512 / NT) k_taylor_sf(const __grid_constant__ RecombParams<T> p) {
     using C = c_t<T>;
     extern __shared__ __align__(16) unsigned char smem[];
     const SFPlan &pl = p.sf;
@@ -172,7 +172,7 @@ __global__ void __launch_bounds__(SF_THREADS, 1) k_taylor_sf(const __grid_consta
     const int tid = threadIdx.x;
 
     // x_a(j) = (lo_a + j + k_a / n_a) / gs_a and the Cartesian q_a(j) = g_a(j) b*_a (0 beyond the box)
-    for (int i = tid; i < 3 * ZR; i += SF_THREADS) {
+    for (int i = tid; i < 3 * ZR; i += NT) {
         const int a = i / ZR, j = i - a * ZR;
         const double gv = (double)(lo[a] + j) + (double)kk[a] / nn[a];
         const bool in = j < nz[a];
@@ -181,7 +181,7 @@ __global__ void __launch_bounds__(SF_THREADS, 1) k_taylor_sf(const __grid_consta
         for (int c = 0; c < 3; ++c) qv[3 * i + c] = in ? (T)(gv * p.recip[3 * a + c]) : T(0);
     }
     // site phases exp(2 pi i H_a r_a) per axis and zone of the box; axis 0 carries b_mu exp(ik.r_mu)
-    for (int i = tid; i < nsite * 3 * ZR; i += SF_THREADS) {
+    for (int i = tid; i < nsite * 3 * ZR; i += NT) {
         const int s = i / (3 * ZR), r = i - s * 3 * ZR, a = r / ZR, j = r - a * ZR;
         const int site = p.site_of[s];
         C v = mk<T>(T(0), T(0));
@@ -194,7 +194,7 @@ __global__ void __launch_bounds__(SF_THREADS, 1) k_taylor_sf(const __grid_consta
         }
         PH[i] = v;
     }
-    for (int i = tid; i < nzone; i += SF_THREADS) Fs[i] = mk<T>(T(0), T(0));
+    for (int i = tid; i < nzone; i += NT) Fs[i] = mk<T>(T(0), T(0));
     __syncthreads();
 
     const size_t nh = g.ncell_h;
@@ -206,7 +206,7 @@ __global__ void __launch_bounds__(SF_THREADS, 1) k_taylor_sf(const __grid_consta
         for (int gi = pl.ngroups - 1; gi >= 0; --gi) {
             const int a0 = pl.a0[gi], a1 = pl.a0[gi + 1];
             // step 1: X[h3][xi(a, b)] = sum_c M'_abc x3^c, one (a, b) chain per slot
-            for (int slot = pl.ibeg[gi] + tid; slot < pl.ibeg[gi + 1]; slot += SF_THREADS) {
+            for (int slot = pl.ibeg[gi] + tid; slot < pl.ibeg[gi + 1]; slot += NT) {
                 const int4 it = pl.items[slot];
                 if (it.x < 0) continue;
                 const int Lc = P - it.x - it.y + 1;
@@ -238,7 +238,7 @@ __global__ void __launch_bounds__(SF_THREADS, 1) k_taylor_sf(const __grid_consta
             __syncthreads();
             // step 2: Y[al][h2][h3] = sum_b X[h3][xi(a, b)] x2^b, one (a, h3) per item
             const int n2it = (a1 - a0) * nz3;
-            for (int i = tid; i < n2it; i += SF_THREADS) {
+            for (int i = tid; i < n2it; i += NT) {
                 const int al = i / nz3, h3 = i - al * nz3;
                 const int a = a0 + al, Lb = P - a + 1;
                 T x2[ZR];
@@ -260,7 +260,7 @@ __global__ void __launch_bounds__(SF_THREADS, 1) k_taylor_sf(const __grid_consta
             }
             __syncthreads();
             // step 3: S(h1) = sum_a Y[a] x1^a for the thread's (h2, h3) columns, continued across groups
-            for (int col = tid; col < ncol; col += SF_THREADS) {
+            for (int col = tid; col < ncol; col += NT) {
                 T x1[ZR];
 #pragma unroll
                 for (int j = 0; j < ZR; ++j) x1[j] = xs[j];
@@ -308,7 +308,7 @@ __global__ void __launch_bounds__(SF_THREADS, 1) k_taylor_sf(const __grid_consta
     const int g01 = gm.g0[0], g02 = gm.g0[1], g03 = gm.g0[2];
     const int c1 = gm.cnt[0], c2 = gm.cnt[1], c3 = gm.cnt[2];
     const size_t nv = (size_t)c1 * c2 * c3;
-    for (int z = tid; z < nzone; z += SF_THREADS) {
+    for (int z = tid; z < nzone; z += NT) {
         const int j = z / ncol, col = z - j * ncol, h2 = col / nz3, h3 = col - h2 * nz3;
         const C Fv = Fs[z];
         const int H1 = lo[0] + j, H2 = lo[1] + h2, H3 = lo[2] + h3;
@@ -333,12 +333,25 @@ __global__ void __launch_bounds__(SF_THREADS, 1) k_taylor_sf(const __grid_consta
     }
 }
 
-template <typename T, int ZR> static void launch_sf(const RecombParams<T> &p, cudaStream_t s) {
+template <typename T, int ZR, int NT> static void launch_sf_nt(const RecombParams<T> &p, cudaStream_t s) {
     const SFLayout L = sf_layout(ZR, p.nsite, p.sf.xpad, p.sf.ymax, p.sf.ngroups, sizeof(c_t<T>));
-    cudaFuncSetAttribute(k_taylor_sf<T, ZR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total);
+    cudaFuncSetAttribute(k_taylor_sf<T, ZR, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total);
     dim3 grid((unsigned)p.g.ncell_h, 2);
-    k_taylor_sf<T, ZR><<<grid, SF_THREADS, L.total, s>>>(p);
+    k_taylor_sf<T, ZR, NT><<<grid, NT, L.total, s>>>(p);
     count_launches(1);
+}
+
+template <typename T, int ZR> static void launch_sf(const RecombParams<T> &p, cudaStream_t s) {
+    if (p.sf.nthr == 128) launch_sf_nt<T, ZR, 128>(p, s);
+    else if (p.sf.nthr == 256) launch_sf_nt<T, ZR, 256>(p, s);
+    else launch_sf_nt<T, ZR, 512>(p, s);
+}
+
+// threads per CTA for a dynamic shared-memory footprint: 16 warps on an SM over the CTAs that fit
+// (228 KB of shared memory per SM, 1 KB of it reserved per CTA)
+int sf_threads_for(size_t smem) {
+    const size_t fit = (228u * 1024u) / (smem + 1024u);
+    return fit >= 4 ? 128 : (fit >= 2 ? 256 : 512);
 }
 
 template <typename T> void recombine_disp_sf(const RecombParams<T> &p, cudaStream_t s) {
@@ -445,7 +458,19 @@ bool taylor_sf_plan(const Geometry &g, const GridMap &gm, int P, int nsite, size
     const int ng = (int)cuts.size() - 1;
     if (ng > SF_MAX_GROUPS) return false;
     pl.ngroups = ng;
+    // footprint of the groups, then the thread count it admits
     int xmax = 0, ymax = 0;
+    for (int gi = 0; gi < ng; ++gi) {
+        int nc = 0;
+        for (int a = cuts[gi]; a < cuts[gi + 1]; ++a) nc += P - a + 1;
+        xmax = std::max(xmax, nc);
+        ymax = std::max(ymax, cuts[gi + 1] - cuts[gi]);
+    }
+    pl.xpad = xmax | 1;
+    pl.ymax = ymax;
+    pl.smem = sf_layout(zr, nsite, pl.xpad, ymax, ng, ce).total;
+    pl.nthr = sf_threads_for(pl.smem);
+    const int NT = pl.nthr;
     items.clear();
     for (int gi = 0; gi < ng; ++gi) {
         const int a0 = cuts[gi], a1 = cuts[gi + 1];
@@ -459,20 +484,15 @@ bool taylor_sf_plan(const Geometry &g, const GridMap &gm, int P, int nsite, size
         std::stable_sort(chain.begin(), chain.end(),
                          [&](const int4 &u, const int4 &v) { return P - u.x - u.y > P - v.x - v.y; });
         const int nc = (int)chain.size();
-        const int rounds = (nc + SF_THREADS - 1) / SF_THREADS;
+        const int rounds = (nc + NT - 1) / NT;
         for (int r = 0; r < rounds; ++r)
-            for (int t = 0; t < SF_THREADS; ++t) {
-                const int si = (r & 1) ? r * SF_THREADS + (SF_THREADS - 1 - t) : r * SF_THREADS + t;
+            for (int t = 0; t < NT; ++t) {
+                const int si = (r & 1) ? r * NT + (NT - 1 - t) : r * NT + t;
                 items.push_back(si < nc ? chain[si] : make_int4(-1, 0, 0, 0));
             }
-        xmax = std::max(xmax, nc);
-        ymax = std::max(ymax, a1 - a0);
     }
     pl.a0[ng] = P + 1;
     pl.ibeg[ng] = (int)items.size();
-    pl.xpad = xmax | 1;
-    pl.ymax = ymax;
-    pl.smem = sf_layout(zr, nsite, pl.xpad, ymax, ng, ce).total;
     pl.items = nullptr;
     return pl.smem <= SF_SMEM_MAX;
 }

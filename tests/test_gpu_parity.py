@@ -432,8 +432,9 @@ def _special_positions_case(kind, nsite, ff, seed, cells=(5, 6, 4), shift=0):
     with periods 4, 3, 2; suffix _xr: random first coordinates), a triclinic cell, two
     supercells and a ragged grid of 6 zones per axis, so that the residue-class recombination
     applies.  The grid is centrosymmetric (the half-grid Friedel mode) unless `shift` moves it by
-    that many voxels along the last axis."""
-    q = syn.QGrid(h0=tuple(-3.0 + 3.0 / n for n in cells[:2]) + (-3.0 + (3.0 + shift) / cells[2],),
+    that many voxels along the last axis (an int) or along each axis (a tuple)."""
+    sh = (0, 0, shift) if np.isscalar(shift) else tuple(shift)
+    q = syn.QGrid(h0=tuple(-3.0 + (3.0 + s) / n for n, s in zip(cells, sh)),
                   step=tuple(1.0 / n for n in cells), count=tuple(6 * n - 5 for n in cells))
     m = syn.small_case(kind, cells=cells, nsite=nsite, nmodels=2, seed=seed, qgrid=q)
     rng = np.random.default_rng(seed)
@@ -488,7 +489,8 @@ def test_residue_classes_special_positions(ctx, prec, tag, disorder, nsite, ff, 
 
 @pytest.mark.parametrize("prec,tag", PREC)
 @pytest.mark.parametrize("cells,shift", [((5, 6, 4), 0), ((4, 6, 5), 0), ((5, 4, 7), 0), ((5, 6, 4), 1),
-                                         ((4, 6, 5), -2)])
+                                         ((4, 6, 5), -2), ((5, 6, 4), (1, -1, 0)), ((4, 6, 5), (2, 0, 1)),
+                                         ((6, 5, 4), (0, 3, -1))])
 @pytest.mark.parametrize("disorder,ff", [(0, "one_j0"), (1, "one_j0"), (1, "mixed")])
 def test_residue_classes_centred_and_shifted_grids(ctx, prec, tag, cells, shift, disorder, ff):
     """Residue-class recombination on centrosymmetric grids with even and odd n3 and on shifted
@@ -499,7 +501,7 @@ def test_residue_classes_centred_and_shifted_grids(ctx, prec, tag, cells, shift,
     got, _ = lm.intensity(qgrid_tuple(m.qgrid), disorder=disorder, mode=1 - disorder, precision=prec)
     fn = core.occupancy_intensity_fft if disorder == 0 else core.magnetic_intensity_fft
     assert rel_err_of_peak(got, fn(m, _G(m), 1 - disorder)) < TOL[tag]
-    if shift == 0:
+    if np.all(np.asarray(shift) == 0):
         assert rel_err_of_peak(got, got[::-1, ::-1, ::-1]) < TOL[tag]
 
 
