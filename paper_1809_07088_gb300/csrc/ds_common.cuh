@@ -95,6 +95,13 @@ __device__ __forceinline__ float exp2_w(float x) {
     return y;
 }
 // 1/x: the SFU's approximate reciprocal (PTX rcp.approx) in FP32, exact division in FP64
+// Programmatic dependent launch.  A kernel that ends a producer stage lets the next kernel of its
+// stream be scheduled early (launch_dependents: no effect unless that kernel was launched with
+// programmatic stream serialization); the consumer runs its independent prologue and then waits
+// (griddep_wait) until the preceding grid has completed and its writes are visible.
+__device__ __forceinline__ void griddep_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory"); }
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
+
 // asynchronous global -> shared copies of BYTES (4, 8 or 16) bytes, in commit groups
 template <int BYTES> __device__ __forceinline__ void cp_async(void *smem, const void *gmem) {
     const unsigned s = (unsigned)__cvta_generic_to_shared(smem);

@@ -164,6 +164,7 @@ template <typename T>
 __global__ void k_fft_columns(Geometry g, FieldSource src, int f0, int cb, const c_t<T> *work, c_t<T> *spec,
                               const c_t<T> *W1g) {
     using C = c_t<T>;
+    griddep_launch_dependents();   // the consumer of the spectra may be scheduled
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int n1 = g.n[0];
     const int ncol = g.n[1] * g.n3h;
@@ -203,6 +204,7 @@ template <typename T>
 __global__ void __launch_bounds__(512) k_fft_field(Geometry g, FieldSource src, int f0, c_t<T> *spec,
                                                    const c_t<T> *W1g, const c_t<T> *W2g, const c_t<T> *W3g) {
     using C = c_t<T>;
+    griddep_launch_dependents();   // the consumer of the spectra may be scheduled
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int n1 = g.n[0], n2 = g.n[1], n3 = g.n[2], n3h = g.n3h;
     const int n2p = (n2 + 1) / 2;
@@ -278,6 +280,7 @@ __global__ void __launch_bounds__(FR_THREADS, 1) k_fft_field_reg(const Geometry 
     constexpr int N3H = N3 / 2 + 1, NROW = N1 * N2, NPAIR = (NROW + 1) / 2, N3P = N3 + 1;
     constexpr int NCELL = N1 * N2 * N3;
     static_assert(NPAIR <= FR_THREADS, "one row pair per thread");
+    griddep_launch_dependents();   // the consumer of the spectra may be scheduled
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C *buf = (C *)smem_raw;          // [N1][N2][N3H]
     T *val = (T *)smem_raw;          // staged field values [row][N3P]

@@ -194,25 +194,62 @@ __global__ void __launch_bounds__(RW_THREADS, sizeof(T) == 4 ? 6 : 3)
 
     // zone phases of the classes (rho1, rho2, rho3) per site.  With one form-factor class the site
     // sum takes every site once in any order: sites by their own index, no sorted-order lookup.
-    for (int i = tid; i < nsite * d23; i += RW_THREADS) {
-        const int s = ax.d23.div(i), r23 = i - s * d23, r2 = ax.d3.div(r23), r3 = r23 - r2 * d3;
-        const C *tH = p.phH + (size_t)s * 3 * nHmax;
-        PW[i] = PK::phase(cmul(tH[rho1], cmul(tH[nHmax + r2], tH[2 * nHmax + r3])));
+    // (the loads of RW_SB entries or sites are issued together, then combined: the staging is
+    // bound by the latency of these loads)
+    constexpr int RW_SB = 4;
+    for (int i0 = tid; i0 < nsite * d23; i0 += RW_SB * RW_THREADS) {
+        C h[RW_SB][3];
+#pragma unroll
+        for (int u = 0; u < RW_SB; ++u) {
+            const int i = i0 + u * RW_THREADS;
+            if (i < nsite * d23) {
+                const int s = ax.d23.div(i), r23 = i - s * d23, r2 = ax.d3.div(r23), r3 = r23 - r2 * d3;
+                const C *tH = p.phH + (size_t)s * 3 * nHmax;
+                h[u][0] = __ldg(tH + rho1);
+                h[u][1] = __ldg(tH + nHmax + r2);
+                h[u][2] = __ldg(tH + 2 * nHmax + r3);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < RW_SB; ++u) {
+            const int i = i0 + u * RW_THREADS;
+            if (i < nsite * d23) PW[i] = PK::phase(cmul(h[u][0], cmul(h[u][1], h[u][2])));
+        }
     }
+    // everything below reads the spectra (and the output): the transform that wrote them, when it
+    // ran just before this kernel, must have completed
+    griddep_wait();
     // y_mu,c(k) = b exp(ik.r_mu) X_mu,c(k) of the thread's k3, every component
     if (tb) {
         // stored half k3 < n3h; the other half from -k with conj (0 <= k_a < n_a)
         const int conj = q3 >= p.g.n3h;
         const int kidx = conj ? (k1m * n2 + k2m) * p.g.n3h + (n3 - q3) : (k1 * n2 + k2) * p.g.n3h + q3;
         const C *spec = p.spec + (size_t)p.model * nsite * NC * nh + kidx;
-        for (int sp = rr; sp < nsite; sp += rs) {
-            const int site = sp;
-            const C *tk = p.phk + (size_t)site * 3 * nmax;
-            const C w = cscale(cmul(cmul(tk[k1], tk[nmax + k2]), tk[2 * nmax + q3]), p.scat[site]);
+        for (int sp0 = rr; sp0 < nsite; sp0 += RW_SB * rs) {
+            C t[RW_SB][3], x[RW_SB][NC];
+            T b[RW_SB];
 #pragma unroll
-            for (int c = 0; c < NC; ++c) {
-                const C x = spec[(size_t)(site * NC + c) * nh];
-                YS[(sp * NC + c) * n3 + q3] = PK::value(cmul(w, conj ? cconj(x) : x));
+            for (int u = 0; u < RW_SB; ++u) {
+                const int sp = sp0 + u * rs;
+                if (sp < nsite) {
+                    const C *tk = p.phk + (size_t)sp * 3 * nmax;
+                    t[u][0] = __ldg(tk + k1);
+                    t[u][1] = __ldg(tk + nmax + k2);
+                    t[u][2] = __ldg(tk + 2 * nmax + q3);
+                    b[u] = __ldg(p.scat + sp);
+#pragma unroll
+                    for (int c = 0; c < NC; ++c) x[u][c] = __ldg(spec + (size_t)(sp * NC + c) * nh);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < RW_SB; ++u) {
+                const int sp = sp0 + u * rs;
+                if (sp < nsite) {
+                    const C w = cscale(cmul(cmul(t[u][0], t[u][1]), t[u][2]), b[u]);
+#pragma unroll
+                    for (int c = 0; c < NC; ++c)
+                        YS[(sp * NC + c) * n3 + q3] = PK::value(cmul(w, conj ? cconj(x[u][c]) : x[u][c]));
+                }
             }
         }
     }
@@ -539,7 +576,19 @@ template <typename T, int NC, int NG, bool ORTHO, bool ACC> static void launch_r
     for (int a = 0; a < 3; ++a) ax.symm &= 2 * p.gm.g0[a] + p.gm.cnt[a] == 1;
     if (L.total > 48 * 1024)
         cudaFuncSetAttribute(k_recomb_rows<T, NC, NG, ORTHO, ACC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total);
-    k_recomb_rows<T, NC, NG, ORTHO, ACC><<<nblk, RW_THREADS, L.total, s>>>(p, ax);
+    // programmatic dependent launch: the CTAs may start (decoding, zone phases) while the
+    // transform before them in the stream finishes; they wait for it before reading its output
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(nblk);
+    cfg.blockDim = dim3(RW_THREADS);
+    cfg.dynamicSmemBytes = L.total;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, k_recomb_rows<T, NC, NG, ORTHO, ACC>, p, ax);
     count_launches(1);
 }
 
