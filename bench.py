@@ -37,8 +37,13 @@ FP32_FMA_LANES_PER_SM, NUM_SMS = 128, 152
 # this workload, from an ncu capture of the current kernel (profiles/); None when the kernel has
 # changed since the capture
 MAG_KERNEL = "k_recomb_rows<float,3,2,true,false>"
-MAG_KERNEL_TRAFFIC = None
-MAG_KERNEL_TRAFFIC_SOURCE = None
+# dram__bytes_read.sum + dram__bytes_write.sum of one launch of the kernel above (ncu --set full,
+# profiles/k_recomb_rows_pyrochlore_20cubed.md): the reads are the spectra read once; the volume
+# written is still in L2 when the kernel ends (written back later, during the next step's flush)
+MAG_KERNEL_TRAFFIC = 1782272 + 1462784
+MAG_KERNEL_TRAFFIC_SOURCE = ("ncu capture of k_recomb_rows<float,3,2,true,false> on this workload: 1.78 MB read "
+                             "(the spectra, once) + 1.46 MB written to DRAM before the kernel ended; the rest of the "
+                             "56 MB volume was still in L2")
 
 
 def workload_config(extra=None):
@@ -325,15 +330,16 @@ def run_ours(args):
             lm_n.intensity(q, out=outs[0], disorder=ds.DS_OCC, mode=ds.DS_DIFFUSE, precision=prec)
             lm_m.intensity(q, out=outs[1], disorder=ds.DS_SPIN, mode=ds.DS_TOTAL, precision=prec)
             return
-        # the two independent volumes on two streams, forked from and joined back to `stream`
-        fork.record(stream)
+        # the two independent volumes on two streams, forked from and joined back to the current one
+        cur = torch.cuda.current_stream(dev)
+        fork.record(cur)
         for s_, j_, (lm_, o_, dis, mode) in zip(side, join, ((lm_n, outs[0], ds.DS_OCC, ds.DS_DIFFUSE),
                                                             (lm_m, outs[1], ds.DS_SPIN, ds.DS_TOTAL))):
             s_.wait_event(fork)
             with torch.cuda.stream(s_):
                 lm_.intensity(q, out=o_, disorder=dis, mode=mode, precision=prec)
             j_.record(s_)
-            stream.wait_event(j_)
+            cur.wait_event(j_)
 
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     clocks = ClockSampler(local)
@@ -342,10 +348,43 @@ def run_ours(args):
         step()
     torch.cuda.synchronize(dev)
 
-    # timed region: K steps, per-step events on the launching stream, L2 flushed in between
     buf = ctypes_buf = None
     import ctypes
     ctypes_buf = ctypes.create_string_buffer(1 << 16)
+
+    # The step as a CUDA graph, captured once after the warm-up: every replay launches the same
+    # kernels on the same resident inputs, and the host enqueues one launch per step, so a delay
+    # on the host (scheduling, the clock sampler) cannot open gaps inside a timed step.  The
+    # replay's volumes are checked bit for bit against a direct run; --no-graph times direct calls.
+    graph, graph_launches, graph_note = None, 0, "direct calls (--no-graph)"
+    if not args.no_graph and side is not None:
+        try:
+            torch.cuda.synchronize(dev)
+            ctx.lib.ds_profile_report(ctx.h, ctypes_buf, len(ctypes_buf))     # reset the launch counter
+            g_ = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g_, capture_error_mode="relaxed"):
+                step()
+            ctx.check(ctx.lib.ds_profile_report(ctx.h, ctypes_buf, len(ctypes_buf)))
+            graph_launches = int(json.loads(ctypes_buf.value.decode()).get("launches", 0))
+            I_n.zero_()
+            I_m.zero_()
+            g_.replay()
+            torch.cuda.synchronize(dev)
+            rn, rm = I_n.clone(), I_m.clone()
+            step()
+            torch.cuda.synchronize(dev)
+            if graph_launches > 0 and torch.equal(rn, I_n) and torch.equal(rm, I_m):
+                graph = g_
+                graph_note = "CUDA graph replay of the step (captured once; %d kernels per step; volumes " \
+                             "identical to direct calls)" % graph_launches
+            else:
+                graph_note = "direct calls (the graph replay did not reproduce the direct volumes)"
+            del rn, rm
+        except Exception as e:  # capture not supported here: time direct calls
+            graph_note = "direct calls (graph capture failed: %s)" % str(e).splitlines()[0][:160]
+            torch.cuda.synchronize(dev)
+
+    # timed region: K steps, per-step events on the launching stream, L2 flushed in between
     ctx.lib.ds_profile_report(ctx.h, ctypes_buf, len(ctypes_buf))     # reset counters
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     barrier(dev)
@@ -354,13 +393,18 @@ def run_ours(args):
     for i in range(args.steps):
         flush.zero_()
         ev[i][0].record(stream)
-        step()
+        if graph is not None:
+            graph.replay()
+        else:
+            step()
         ev[i][1].record(stream)
     torch.cuda.synchronize(dev)
     barrier(dev)
     t_wall = time.perf_counter() - t_wall
     ctx.check(ctx.lib.ds_profile_report(ctx.h, ctypes_buf, len(ctypes_buf)))
     timed_launches = int(json.loads(ctypes_buf.value.decode()).get("launches", 0))
+    if graph is not None:
+        timed_launches = graph_launches * args.steps
     clk = clocks.stop()
     # per-stage times from the same steps run again with the library's stage events: the events
     # sit between the kernels of a stream (no launch overlap), so they stay out of the timed region
@@ -495,7 +539,7 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": workload_config({"parallelism": "replicas" if ws > 1 else "single GPU",
-                                       "streams": args.streams}),
+                                       "streams": args.streams, "launch": graph_note}),
             "max_rel_err_vs_fp64": max(errs), "fp64_plain": {"ms_per_step": ms64, "value": ws * vox_step / (ms64 / 1e3)},
             "e2e": e2e, "roofline": roofline, "stages": stages, "gpu_launches": timed_launches,
             "wall_ms_per_step": 1e3 * t_wall / args.steps, "clocks": clk, "cpu_baseline": cpu,
@@ -1063,6 +1107,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serving", type=int, default=512, help="requests in the serving stream (0 = skip)")
     ap.add_argument("--no-rows", action="store_true", help="skip the per-row measurements")
+    ap.add_argument("--no-graph", action="store_true", help="time direct calls instead of a replayed CUDA graph")
     ap.add_argument("--profile-workload", choices=["taylor", "lanczos", "subbox", "subbox_dft", "dw"], default=None,
                     help="run one small row workload twice (for ncu captures) and exit")
     ap.add_argument("--streams", type=int, default=2, choices=[1, 2],

@@ -76,6 +76,16 @@ void lattice_matrices(const double lat[6], double A[9], double B[9]) {
         for (int j = 0; j < 3; ++j) B[3 * i + j] = two_pi * inv[3 * j + i];
 }
 
+// order the stream after an event, unless the event's work has already completed (then the wait
+// is a no-op; skipping it also keeps a request capturable into a CUDA graph when the event was
+// recorded before the capture began)
+static cudaError_t wait_unless_done(cudaStream_t st, cudaEvent_t ev) {
+    const cudaError_t q = cudaEventQuery(ev);
+    if (q == cudaSuccess) return cudaSuccess;
+    if (q != cudaErrorNotReady) return q;
+    return cudaStreamWaitEvent(st, ev, 0);
+}
+
 static bool plan_axis(int n, AxisPlan &p) {
     p.n = n;
     p.nrad = 0;
@@ -749,7 +759,7 @@ ds_status queue_corner_xmax(ds_model *M, const ds_qgrid *q, const ds_opts *o, cu
     }
     Corners corners;
     box_corners(M, eg0, ecnt, corners.v);
-    if (M->ready) CK(cudaStreamWaitEvent(st, M->ready, 0));
+    if (M->ready) CK(wait_unless_done(st, M->ready));
     double *d_x = (double *)ws.get(sizeof(double) * 9);
     if (ws.failed) return ds_fail(ctx, DS_ERR_OOM, "device allocation failed");
     const size_t natom = (size_t)M->nmodels * M->nsite * M->n[0] * M->n[1] * M->n[2];
@@ -834,7 +844,7 @@ ds_status site_tables(ds_model *M, const Geometry &g, const GridMap &gm, int nma
     std::lock_guard<std::mutex> lk(M->cache_mu);
     auto it = M->site_tables.find(key);
     if (it != M->site_tables.end()) {
-        CK(cudaStreamWaitEvent(st, it->second.done, 0));
+        CK(wait_unless_done(st, it->second.done));
         *phk = (const C *)it->second.phk;
         *phH = (const C *)it->second.phH;
         return DS_OK;
@@ -869,7 +879,7 @@ ds_status plan_and_run(ds_model *M, const ds_qgrid *q, const ds_opts *o, T *d_ou
     int g0[3], cnt[3];
     ds_status rc = grid_indices(ctx, M, q, g0, cnt);
     if (rc != DS_OK) return rc;
-    if (M->ready) CK(cudaStreamWaitEvent(st, M->ready, 0));  // uploads made on another stream
+    if (M->ready) CK(wait_unless_done(st, M->ready));  // uploads made on another stream
     Geometry g;
     make_geometry(M->n, g);
     const int nsite = M->nsite, nmod = M->nmodels;

@@ -127,61 +127,82 @@ __global__ void __launch_bounds__(256) k_lanczos_mid(const T *__restrict__ in, T
 }
 
 // Fused in-plane pass over [A][B][C] (C contiguous): out[a][b][c] = sum_s w_s sum_t w_t
-// in[a][b + s][c + t] for b < B - 2h, c < C - 2h.  A CTA owns a segment of 256 outputs along C and
-// a run of L outputs along B of one a; it streams the run's L + NT - 1 input rows through a ring
-// of LP_D row buffers in shared memory, filled by asynchronous copies LP_D - 1 rows ahead (one
-// barrier per row).  Every thread forms the axis-C stencil of a staged row at its column and
-// keeps the last NT such values in registers, from which the axis-B stencil gives one output row
-// per input row.
-constexpr int LP_D = 8;
+// in[a][b + s][c + t] for b < B - 2h, c < C - 2h.  A CTA owns a segment of W = 2 x blockDim
+// outputs along C and a run of L outputs along B of one a; it streams the run's L + NT - 1 input
+// rows through a ring of D row buffers in shared memory, filled by asynchronous copies D - 1 rows
+// ahead (one barrier per row).  Each thread forms the axis-C stencil at its two adjacent columns
+// from 16 staged values and keeps, per column, the last NT such values in registers, from which
+// the axis-B stencil gives one output row per input row.  The row loop is unrolled by D, a
+// multiple of NT, so both rings are indexed by constants.
+template <int NT> constexpr int plane_depth() { return NT * ((8 + NT - 1) / NT); }
 template <typename T, int NT>
-__global__ void __launch_bounds__(256) k_lanczos_plane(const T *__restrict__ in, T *__restrict__ out, int A, int B,
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 3) k_lanczos_plane(const T *__restrict__ in, T *__restrict__ out, int A, int B,
                                                        int C, int L, const __grid_constant__ Taps<T> tp) {
-    constexpr int TC = 256, W = TC + NT - 1;
-    __shared__ __align__(16) T buf[LP_D][W];
-    const int tid = threadIdx.x;
+    constexpr int D = plane_depth<NT>();
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *buf = (T *)smem_raw;
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    const int W = 2 * nthr, SW = W + NT + 1;   // staged width of a row (even: 8- and 16-byte loads)
     const int Bo = B - (NT - 1), Co = C - (NT - 1);
     const int nrun = (Bo + L - 1) / L;
     const int a = blockIdx.y / nrun, run = blockIdx.y - a * nrun;
-    const int c0 = blockIdx.x * TC;
+    const int c0 = blockIdx.x * W;
     const int b0 = run * L, b1 = min(Bo, b0 + L);
-    const int nw = min(W, C - c0);          // staged inputs of a row segment
+    const int nw = min(W + NT - 1, C - c0);     // staged inputs of a row segment
     const T *src = in + ((size_t)a * B + b0) * C + c0;
-    T *dst = out + ((size_t)a * Bo + b0) * Co + c0 + tid;
-    const bool act = c0 + tid < Co;
+    T *dst = out + ((size_t)a * Bo + b0) * Co + c0 + 2 * tid;
+    const bool act0 = c0 + 2 * tid < Co, act1 = c0 + 2 * tid + 1 < Co;
     const int nrow = b1 - b0 + NT - 1;
-    // row i of the run into buffer i mod LP_D (one commit group per row, empty past the run)
-    auto issue = [&](int i) {
+    // row i of the run into buffer `slot` (one commit group per row, empty past the run)
+    auto issue = [&](int i, int slot) {
         if (i < nrow) {
             const T *row = src + (size_t)i * C;
-            T *sb = buf[i % LP_D];
-            for (int j = tid; j < nw; j += TC) cp_async<sizeof(T)>(sb + j, row + j);
+            T *sb = buf + slot * SW;
+            for (int j = tid; j < nw; j += nthr) cp_async<sizeof(T)>(sb + j, row + j);
         }
         cp_async_commit();
     };
 #pragma unroll
-    for (int i = 0; i < LP_D - 1; ++i) issue(i);
-    T ring[NT];
+    for (int u = 0; u < D - 1; ++u) issue(u, u);
+    T r0[NT], r1[NT];   // the last NT axis-C values of the two columns (slot = row mod NT)
 #pragma unroll
-    for (int t = 0; t < NT; ++t) ring[t] = T(0);
-    for (int i = 0; i < nrow; ++i) {
-        cp_async_wait<LP_D - 2>();   // row i has landed (this thread's copies)
-        __syncthreads();             // every thread's copies of row i; row i - 1 is no longer read
-        issue(i + LP_D - 1);         // into the buffer row i - 1 used
-        const T *sb = buf[i % LP_D];
-        T x = T(0);
-        if (act) {
+    for (int t = 0; t < NT; ++t) r0[t] = r1[t] = T(0);
+    for (int i0 = 0; i0 < nrow; i0 += D) {
 #pragma unroll
-            for (int t = 0; t < NT; ++t) x = fma(tp.w[t], sb[tid + t], x);
-        }
+        for (int u = 0; u < D; ++u) {
+            const int i = i0 + u;
+            if (i >= nrow) break;
+            cp_async_wait<D - 2>();   // row i has landed (this thread's copies)
+            __syncthreads();          // every thread's copies of row i; row i - 1 is no longer read
+            issue(i + D - 1, (u + D - 1) % D);
+            const T *sb = buf + u * SW + 2 * tid;
+            T v[NT + 1];
 #pragma unroll
-        for (int t = 0; t < NT - 1; ++t) ring[t] = ring[t + 1];
-        ring[NT - 1] = x;
-        if (i >= NT - 1 && act) {
-            T acc = T(0);
+            for (int q = 0; q < (NT + 1) / 2; ++q) {
+                if constexpr (sizeof(T) == 4) {
+                    const float2 p2 = ((const float2 *)sb)[q];
+                    v[2 * q] = p2.x, v[2 * q + 1] = p2.y;
+                } else {
+                    v[2 * q] = sb[2 * q], v[2 * q + 1] = sb[2 * q + 1];
+                }
+            }
+            T x0 = T(0), x1 = T(0);
 #pragma unroll
-            for (int t = 0; t < NT; ++t) acc = fma(tp.w[t], ring[t], acc);
-            dst[(size_t)(i - (NT - 1)) * Co] = acc;
+            for (int t = 0; t < NT; ++t) x0 = fma(tp.w[t], v[t], x0), x1 = fma(tp.w[t], v[t + 1], x1);
+            r0[u % NT] = x0;
+            r1[u % NT] = x1;
+            if (i >= NT - 1) {
+                T y0 = T(0), y1 = T(0);
+#pragma unroll
+                for (int t = 0; t < NT; ++t) {
+                    const int sl = (u + 1 + t) % NT;   // row i - NT + 1 + t, oldest first
+                    y0 = fma(tp.w[t], r0[sl], y0);
+                    y1 = fma(tp.w[t], r1[sl], y1);
+                }
+                T *o = dst + (size_t)(i - (NT - 1)) * Co;
+                if (act0) o[0] = y0;
+                if (act1) o[1] = y1;
+            }
         }
     }
     cp_async_wait<0>();
@@ -201,14 +222,19 @@ static void sliding_passes(const T *ext, T *tmp1, T *tmp2, T *out, int d[3], con
         const int maxrun = std::max(1, 65535 / A);
         return std::max(L, (Bo + maxrun - 1) / maxrun);
     };
-    // axes 2 and 1 fused: [d0][d1][d2] -> [d0][d1 - 2h][d2 - 2h]
+    // axes 2 and 1 fused: [d0][d1][d2] -> [d0][d1 - 2h][d2 - 2h]; segments of at most 512
+    // outputs along C, as equal as whole warps (two outputs per thread) allow
     {
         const int Bo = d[1] - 2 * h, Co = d[2] - 2 * h;
-        const long long nseg = (Co + 255) / 256;
+        const int nseg = (Co + 511) / 512;
+        const int per = (Co + nseg - 1) / nseg;
+        const int nthr = 32 * ((per + 63) / 64);
         const int L = run_len(nseg, d[0], Bo);
         const int nrun = (Bo + L - 1) / L;
-        dim3 grid((unsigned)nseg, (unsigned)(d[0] * nrun));
-        k_lanczos_plane<T, NT><<<grid, 256, 0, s>>>(ext, tmp1, d[0], d[1], d[2], L, tp);
+        const size_t sm = (size_t)plane_depth<NT>() * (2 * nthr + NT + 1) * sizeof(T);
+        if (sm > 48 * 1024) cudaFuncSetAttribute(k_lanczos_plane<T, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        dim3 grid((unsigned)((Co + 2 * nthr - 1) / (2 * nthr)), (unsigned)(d[0] * nrun));
+        k_lanczos_plane<T, NT><<<grid, nthr, sm, s>>>(ext, tmp1, d[0], d[1], d[2], L, tp);
         d[1] = Bo;
         d[2] = Co;
     }
