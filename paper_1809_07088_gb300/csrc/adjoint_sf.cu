@@ -105,7 +105,18 @@ __global__ void __launch_bounds__(AS_THREADS, 512 / AS_THREADS)
         const int G1 = n1 * (lo[0] + j) + kk[0], G2 = n2 * (lo[1] + h2) + kk[1], G3 = n3 * (lo[2] + h3) + kk[2];
         const size_t v = ((size_t)(G1 - gm.g0[0]) * gm.cnt[1] + (G2 - gm.g0[1])) * gm.cnt[2] + (G3 - gm.g0[2]);
         const float2 Fv = F[(size_t)p.model * nv + v];
-        const float gI = dLdI[v] * scale;
+        float gI = dLdI[v] * scale;
+        if (p.ff.ncls == 1) {
+            // one form-factor class: f(|G|) enters every beta of the zone, folded in here once
+            float Q[3];
+#pragma unroll
+            for (int a = 0; a < 3; ++a)
+                Q[a] = fmaf((float)G1, p.qstep[a], fmaf((float)G2, p.qstep[3 + a], (float)G3 * p.qstep[6 + a]));
+            const float q2 = Q[0] * Q[0] + Q[1] * Q[1] + Q[2] * Q[2];
+            float f = p.ff.cls_gc[0];
+            for (int i = 0; i < p.ff.cls_ng[0]; ++i) f = fmaf(p.ff.cls_ga[0][i], exp2_w(p.ff.cls_gb[0][i] * q2), f);
+            gI *= f;
+        }
         gam[z] = make_float2(gI * Fv.x, -gI * Fv.y);
     }
     __syncthreads();
@@ -122,14 +133,17 @@ __global__ void __launch_bounds__(AS_THREADS, 512 / AS_THREADS)
             const float2 pk = cscale(cmul(cmul(tk[kk[0]], tk[p.nmax + kk[1]]), tk[2 * p.nmax + kk[2]]), p.scat[site]);
             for (int z = tid; z < nzone; z += AS_THREADS) {
                 const int j = z / ncol, col = z - j * ncol, h2 = col / nz3, h3 = col - h2 * nz3;
-                const int G1 = n1 * (lo[0] + j) + kk[0], G2 = n2 * (lo[1] + h2) + kk[1], G3 = n3 * (lo[2] + h3) + kk[2];
-                float Q[3];
+                float f = 1.f;
+                if (p.ff.ncls != 1) {
+                    const int G1 = n1 * (lo[0] + j) + kk[0], G2 = n2 * (lo[1] + h2) + kk[1], G3 = n3 * (lo[2] + h3) + kk[2];
+                    float Q[3];
 #pragma unroll
-                for (int a = 0; a < 3; ++a)
-                    Q[a] = fmaf((float)G1, p.qstep[a], fmaf((float)G2, p.qstep[3 + a], (float)G3 * p.qstep[6 + a]));
-                const float q2 = Q[0] * Q[0] + Q[1] * Q[1] + Q[2] * Q[2];
-                float f = p.ff.cls_gc[cls];
-                for (int i = 0; i < p.ff.cls_ng[cls]; ++i) f = fmaf(p.ff.cls_ga[cls][i], exp2_w(p.ff.cls_gb[cls][i] * q2), f);
+                    for (int a = 0; a < 3; ++a)
+                        Q[a] = fmaf((float)G1, p.qstep[a], fmaf((float)G2, p.qstep[3 + a], (float)G3 * p.qstep[6 + a]));
+                    const float q2 = Q[0] * Q[0] + Q[1] * Q[1] + Q[2] * Q[2];
+                    f = p.ff.cls_gc[cls];
+                    for (int i = 0; i < p.ff.cls_ng[cls]; ++i) f = fmaf(p.ff.cls_ga[cls][i], exp2_w(p.ff.cls_gb[cls][i] * q2), f);
+                }
                 const float2 ph = cmul(cmul(tH[lo[0] + j - gm.Hmin[0]], tH[p.nHmax + lo[1] + h2 - gm.Hmin[1]]),
                                        tH[2 * p.nHmax + lo[2] + h3 - gm.Hmin[2]]);
                 bv[z] = cmul(gam[z], cscale(cmul(ph, pk), f));

@@ -198,6 +198,7 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_taylor_sf(const __grid_constan
     __syncthreads();
 
     const size_t nh = g.ncell_h;
+    const bool one_ff = p.ff.ncls == 1;
     int cls = 0;
     for (int s = 0; s < nsite; ++s) {
         if (s == p.ff.cls_end[cls]) ++cls;
@@ -279,10 +280,19 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_taylor_sf(const __grid_constan
                         if (j < nz1) Ss[j * ncol + col] = Sv[j];
                     continue;
                 }
-                // F += b f(|Q|) exp(iG.r_mu) S at the zones of this column
+                // F += b f(|Q|) exp(iG.r_mu) S at the zones of this column (with one form-factor class
+                // f multiplies the site sum once, in the epilogue)
                 const int h2 = col / nz3, h3 = col - h2 * nz3;
                 const C *ph = PH + (size_t)s * 3 * ZR;
                 const C p23 = cmul(ph[ZR + h2], ph[2 * ZR + h3]);
+                if (one_ff) {
+#pragma unroll
+                    for (int j = 0; j < ZR; ++j) {
+                        if (j >= nz1) break;
+                        cfma(Fs[j * ncol + col], cmul(ph[j], p23), Sv[j]);
+                    }
+                    continue;
+                }
                 T q23[3];
 #pragma unroll
                 for (int c = 0; c < 3; ++c) q23[c] = qv[3 * (ZR + h2) + c] + qv[3 * (2 * ZR + h3) + c];
@@ -310,7 +320,17 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_taylor_sf(const __grid_constan
     const size_t nv = (size_t)c1 * c2 * c3;
     for (int z = tid; z < nzone; z += NT) {
         const int j = z / ncol, col = z - j * ncol, h2 = col / nz3, h3 = col - h2 * nz3;
-        const C Fv = Fs[z];
+        C Fv = Fs[z];
+        if (one_ff) {
+            // the common form factor f(|Q|) of the zone
+            T Q[3];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) Q[c] = qv[3 * j + c] + qv[3 * (ZR + h2) + c] + qv[3 * (2 * ZR + h3) + c];
+            const T q2 = Q[0] * Q[0] + Q[1] * Q[1] + Q[2] * Q[2];
+            T f = p.ff.cls_gc[0];
+            for (int i = 0; i < p.ff.cls_ng[0]; ++i) f += p.ff.cls_ga[0][i] * exp2_w(p.ff.cls_gb[0][i] * q2);
+            Fv = cscale(Fv, f);
+        }
         const int H1 = lo[0] + j, H2 = lo[1] + h2, H3 = lo[2] + h3;
         const int G1 = n1 * H1 + k1, G2 = n2 * H2 + k2, G3 = n3 * H3 + k3;
         if (wd && G1 >= g01 && G1 < g01 + c1 && G2 >= g02 && G2 < g02 + c2 && G3 >= g03 && G3 < g03 + c3) {
