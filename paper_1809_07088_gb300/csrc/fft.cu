@@ -384,6 +384,189 @@ static bool fft_field_reg(const Geometry &g, const FieldSource &src, int f0, int
     }
 }
 
+// ---- 64-point lines over eight threads (FP32 supercells of 64 cells per axis) -----------------
+// X[k1 + 8 k2] = sum_t w64^(t k1) w8^(t k2) sum_m x[t + 8 m] w8^(m k1) (w_N = exp(+2 pi i / N)):
+// thread t of a line holds x[t + 8 m], m < 8, runs the inner 8-point DFT in registers, multiplies
+// by its own twiddles w64^(t k1), and the eight threads exchange values through a warp-private
+// shared area so that thread k1 holds the inner results of every t; a second 8-point DFT leaves
+// X[k1 + 8 k2], k2 < 8, in thread k1.  The area holds 8 rows of 9 complex per line (lines 72 apart):
+// the writes and the reads of a warp each take the minimum two shared-memory wavefronts.
+constexpr int F64_LS = 72, F64_RS = 9;
+template <typename T>
+__device__ __forceinline__ void fft64_line(c_t<T> (&v)[8], const c_t<T> (&tw)[8], c_t<T> *area, int t) {
+    RegFFT<T, 8>::run(v);
+#pragma unroll
+    for (int k1 = 1; k1 < 8; ++k1) v[k1] = cmul(v[k1], tw[k1]);
+#pragma unroll
+    for (int k1 = 0; k1 < 8; ++k1) area[k1 * F64_RS + t] = v[k1];
+    __syncwarp();
+#pragma unroll
+    for (int u = 0; u < 8; ++u) v[u] = area[t * F64_RS + u];
+    __syncwarp();   // the area may be written again
+    RegFFT<T, 8>::run(v);
+}
+// the 64th roots of unity, computed by the compiler (exact octant reduction, Taylor series of the
+// remainder) and rounded to FP32 once
+struct Roots64 {
+    float c[64], s[64];
+};
+constexpr Roots64 make_roots64() {
+    Roots64 r{};
+    for (int m = 0; m < 64; ++m) {
+        r.c[m] = (float)root_cs(64, m, 0);
+        r.s[m] = (float)root_cs(64, m, 1);
+    }
+    return r;
+}
+__constant__ Roots64 c_roots64 = make_roots64();
+// w64^(t k1), k1 < 8
+template <typename T> __device__ __forceinline__ void fft64_twiddles(int t, c_t<T> (&tw)[8]) {
+#pragma unroll
+    for (int k1 = 0; k1 < 8; ++k1) {
+        const int m = (t * k1) & 63;
+        tw[k1] = mk<T>((T)c_roots64.c[m], (T)c_roots64.s[m]);
+    }
+}
+
+// Axes 3 and 2 of one 64 x 64 plane (r1 = blockIdx mod 64) of field f0 + blockIdx / 64: axis 3 on
+// 32 complex lines that pack rows 2p (real) and 2p + 1 (imaginary), separated into the half spectra
+// of the two rows (k3 <= 32), then axis 2 on the 33 columns; the plane [k2][k3] is written to the
+// work buffer with coalesced stores.  256 threads: eight per line, four lines per warp.
+template <typename T>
+__global__ void __launch_bounds__(256) k_fft_planes64(const FieldSource src, int f0, c_t<T> *work) {
+    using C = c_t<T>;
+    constexpr int N = 64, NH = 33, PS = NH + 1;   // plane row stride (padded)
+    __shared__ __align__(16) C tr[8][4][F64_LS];
+    __shared__ __align__(16) C pl[N * PS];
+    const int tid = threadIdx.x, warp = tid >> 5, lw = (tid >> 3) & 3, t = tid & 7;
+    const int line = warp * 4 + lw;
+    C *area = &tr[warp][lw][0];
+    C tw[8];
+    fft64_twiddles<T>(t, tw);
+    const int fl = blockIdx.x >> 6, r1 = blockIdx.x & 63, f = f0 + fl;
+    const FieldRow<T> fr = field_row<T>(src, N * N * N, f);
+    // the plane's 64 x 64 values, staged in the plane buffer with four cells per load (rows of 68:
+    // the four lines of a warp read disjoint banks)
+    constexpr int SR = 68;
+    static_assert(N * SR * sizeof(T) <= N * PS * sizeof(C), "staging fits the plane buffer");
+    T *stage = (T *)pl;
+    for (int c4 = tid; c4 < N * N / 4; c4 += 256) {
+        const int cell = r1 * N * N + 4 * c4, g4 = cell >> 2;
+        T x[4];
+        if (fr.kind == SRC_DISP) {
+            const float4 a = ((const float4 *)fr.pw[0])[g4], b = ((const float4 *)fr.pw[1])[g4],
+                         d = ((const float4 *)fr.pw[2])[g4];
+            x[0] = a.x * b.x * d.x, x[1] = a.y * b.y * d.y, x[2] = a.z * b.z * d.z, x[3] = a.w * b.w * d.w;
+            if (fr.occ) {
+                const uchar4 o = ((const uchar4 *)fr.occ)[g4];
+                x[0] *= (T)o.x, x[1] *= (T)o.y, x[2] *= (T)o.z, x[3] *= (T)o.w;
+            }
+        } else if (fr.kind == SRC_OCC) {
+            const uchar4 o = ((const uchar4 *)fr.occ)[g4];
+            x[0] = (T)o.x - fr.mean, x[1] = (T)o.y - fr.mean, x[2] = (T)o.z - fr.mean, x[3] = (T)o.w - fr.mean;
+        } else {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) x[q] = row_value<T>(fr, cell + q);
+        }
+        const int row = (4 * c4) >> 6, col = (4 * c4) & 63;
+        *(float4 *)(stage + row * SR + col) = make_float4(x[0], x[1], x[2], x[3]);
+    }
+    __syncthreads();
+    // axis 3 on the packed rows 2 line, 2 line + 1
+    C v[8];
+#pragma unroll
+    for (int m = 0; m < 8; ++m) v[m] = mk<T>(stage[(2 * line) * SR + t + 8 * m], stage[(2 * line + 1) * SR + t + 8 * m]);
+    __syncthreads();   // the plane buffer is written below
+    fft64_line<T>(v, tw, area, t);   // v[k2] = Z[t + 8 k2]
+    // X = (Z_k + conj Z_-k) / 2 (row 2 line), Y = (Z_k - conj Z_-k) / (2i) (row 2 line + 1), k <= 32
+#pragma unroll
+    for (int k2 = 0; k2 < 8; ++k2) area[t + 8 * k2] = v[k2];
+    __syncwarp();
+#pragma unroll
+    for (int k2 = 0; k2 < 5; ++k2) {
+        const int k = t + 8 * k2;
+        if (k <= 32) {
+            const C zk = v[k2], zm = area[(N - k) & (N - 1)];
+            pl[(2 * line) * PS + k] = mk<T>(T(0.5) * (zk.x + zm.x), T(0.5) * (zk.y - zm.y));
+            pl[(2 * line + 1) * PS + k] = mk<T>(T(0.5) * (zk.y + zm.y), T(-0.5) * (zk.x - zm.x));
+        }
+    }
+    __syncthreads();
+    // axis 2 on the columns k3 (33 lines: the last one by warp 0's first eight threads)
+    for (int rep = 0; rep < 2; ++rep) {
+        if (rep == 1 && warp != 0) break;
+        const int L = line + 32 * rep;
+        const bool act = L < NH;
+        C w[8];
+#pragma unroll
+        for (int m = 0; m < 8; ++m) w[m] = act ? pl[(t + 8 * m) * PS + L] : mk<T>(T(0), T(0));
+        fft64_line<T>(w, tw, area, t);
+        if (act) {
+#pragma unroll
+            for (int k2 = 0; k2 < 8; ++k2) pl[(t + 8 * k2) * PS + L] = w[k2];
+        }
+    }
+    __syncthreads();
+    C *out = work + (size_t)blockIdx.x * (N * NH);
+    for (int i = tid; i < N * NH; i += 256) {
+        const int k2 = i / NH, k3 = i - k2 * NH;
+        out[i] = pl[k2 * PS + k3];
+    }
+}
+
+// Axis 1 of 32 columns (k2, k3) of one field's work planes: the 64 x 32 block is read with
+// coalesced rows, transformed by eight threads per column, and the half spectrum written with
+// coalesced rows (times i^n for Taylor monomials).
+template <typename T>
+__global__ void __launch_bounds__(256) k_fft_columns64(const FieldSource src, int f0, const c_t<T> *work,
+                                                       c_t<T> *spec) {
+    using C = c_t<T>;
+    constexpr int N = 64, NCOL = 64 * 33, CB = 32, CS = CB + 1, NCH = NCOL / CB;
+    griddep_launch_dependents();   // the consumer of the spectra may be scheduled
+    __shared__ __align__(16) C tr[8][4][F64_LS];
+    __shared__ __align__(16) C cb[N * CS];
+    const int tid = threadIdx.x, warp = tid >> 5, lw = (tid >> 3) & 3, t = tid & 7;
+    const int line = warp * 4 + lw;
+    C *area = &tr[warp][lw][0];
+    C tw[8];
+    fft64_twiddles<T>(t, tw);
+    const int fl = blockIdx.x / NCH, c0 = (blockIdx.x - fl * NCH) * CB, f = f0 + fl;
+    const C *in = work + (size_t)fl * N * NCOL + c0;
+    for (int i = tid; i < N * CB; i += 256) {
+        const int r = i >> 5, c = i & (CB - 1);
+        cb[r * CS + c] = in[(size_t)r * NCOL + c];
+    }
+    __syncthreads();
+    C v[8];
+#pragma unroll
+    for (int m = 0; m < 8; ++m) v[m] = cb[(t + 8 * m) * CS + line];
+    fft64_line<T>(v, tw, area, t);
+#pragma unroll
+    for (int k2 = 0; k2 < 8; ++k2) cb[(t + 8 * k2) * CS + line] = v[k2];
+    __syncthreads();
+    int rot = 0;
+    if (src.kind == SRC_DISP) rot = src.terms[(f % src.nf_per_model) % src.T].w;
+    C *out = spec + (size_t)f * (N * NCOL) + c0;
+    for (int i = tid; i < N * CB; i += 256) {
+        const int k1 = i >> 5, c = i & (CB - 1);
+        out[(size_t)k1 * NCOL + c] = cipow(cb[k1 * CS + c], rot);
+    }
+}
+
+template <typename T>
+static bool fft_lines64(const Geometry &g, const FieldSource &src, int f0, int nf, c_t<T> *work, c_t<T> *spec,
+                        cudaStream_t s) {
+    if constexpr (sizeof(T) != 4) {
+        return false;
+    } else {
+        if (g.n[0] != 64 || g.n[1] != 64 || g.n[2] != 64 || (size_t)nf * 64 >= (1u << 31)) return false;
+        k_fft_planes64<T><<<(unsigned)(nf * 64), 256, 0, s>>>(src, f0, work);
+        k_fft_columns64<T><<<(unsigned)(nf * 66), 256, 0, s>>>(src, f0, work, spec);
+        count_launches(2);
+        return true;
+    }
+}
+
 // shared memory of the whole-field kernel (0 when a field does not fit)
 static size_t field_smem(const Geometry &g, size_t ce) {
     const int n2p = (g.n[1] + 1) / 2;
@@ -437,6 +620,7 @@ template <typename T>
 void fft_real_fields(const Geometry &g, const FieldSource &src, int f0, int nf, c_t<T> *work, c_t<T> *spec,
                      const c_t<T> *W1, const c_t<T> *W2, const c_t<T> *W3, cudaStream_t s) {
     if (fft_field_reg<T>(g, src, f0, nf, spec, s)) return;
+    if (fft_lines64<T>(g, src, f0, nf, work, spec, s)) return;
     // whole-field kernel: for batches large enough to fill the GPU with one CTA per field, on
     // supercells of at least 18^3 cells (measured on GB300: 1.4x faster than the two passes at
     // 20^3 x 1024 fields, even at 16^3 x 2000, slower for 8^3 or for fewer fields)

@@ -135,12 +135,13 @@ def test_fft_sizes_all_radices(ctx, cells):
     assert rel_err_of_peak(got, want) < TOL["fp64"]
 
 
-@pytest.mark.parametrize("n", [8, 16, 20, 32])
+@pytest.mark.parametrize("n", [8, 16, 20, 32, 64])
 @pytest.mark.parametrize("kind", [0, 1, 2])
 def test_fft_register_kernel_cubic_sizes(ctx, n, kind):
-    """Cubic FP32 supercells of 8, 16, 20 and 32 cells (one CTA per field, lines in registers):
-    occupancy, moments and Taylor monomials (the i^n factor of every order), two supercells, against
-    the oracle's FFT method."""
+    """Cubic FP32 supercells of 8, 16, 20 and 32 cells (one CTA per field, lines in registers) and of
+    64 cells (planes, then columns, each 64-point line split over eight threads): occupancy, moments
+    and Taylor monomials (the i^n factor of every order), two supercells, against the oracle's FFT
+    method."""
     q = syn.QGrid(h0=(-1.0 - 2.0 / n,) * 3, step=(1.0 / n,) * 3, count=(n + 5, n + 3, 2 * n + 1))
     m = syn.small_case(kind, cells=(n, n, n), nsite=2, nmodels=2, seed=600 + n + kind, qgrid=q)
     lm = to_library(ctx, m)
