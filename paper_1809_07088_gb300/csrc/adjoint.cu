@@ -23,6 +23,7 @@
 #include <vector>
 
 #include "api_internal.h"
+#include "fft_reg.cuh"
 #include "internal.h"
 
 using namespace ds;
@@ -96,10 +97,73 @@ __global__ void k_fft_columns_re(Geometry g, int f0, int cb, const c_t<T> *work,
     }
 }
 
+// FP32 fields of 32^3 cells: lines of 32 points in one thread's registers (compile-time twiddles).
+// Planes: a CTA stages four 32 x 32 planes (rows padded to 33: conflict-free rows and columns), a
+// warp transforms one plane, a thread a row (axis 3) and then a column (axis 2).
+constexpr int C32_PP = 4;
+template <typename T>
+__global__ void __launch_bounds__(128) k_fft_planes_c32(const c_t<T> *in, int f0, c_t<T> *work) {
+    using C = c_t<T>;
+    constexpr int N = 32, RS = N + 1;
+    __shared__ __align__(16) C buf[C32_PP * N * RS];
+    const int tid = threadIdx.x, q = tid >> 5, l = tid & 31;
+    const size_t p0 = (size_t)blockIdx.x * C32_PP;   // first plane (field, k1) of the batch
+    const C *src = in + ((size_t)f0 * N + p0) * N * N;
+    for (int i = tid; i < C32_PP * N * N; i += 128) buf[(i >> 5) * RS + (i & 31)] = src[i];
+    __syncthreads();
+    C a[N];
+    C *row = buf + (q * N + l) * RS;
+#pragma unroll
+    for (int j = 0; j < N; ++j) a[j] = row[j];
+    RegFFT<T, N>::run(a);
+#pragma unroll
+    for (int j = 0; j < N; ++j) row[j] = a[j];
+    __syncwarp();   // the plane's rows are complete (one warp per plane)
+    C *col = buf + q * N * RS + l;
+#pragma unroll
+    for (int j = 0; j < N; ++j) a[j] = col[j * RS];
+    RegFFT<T, N>::run(a);
+#pragma unroll
+    for (int j = 0; j < N; ++j) col[j * RS] = a[j];
+    __syncthreads();
+    C *dst = work + p0 * N * N;
+    for (int i = tid; i < C32_PP * N * N; i += 128) dst[i] = buf[(i >> 5) * RS + (i & 31)];
+}
+// Columns: a thread transforms one axis-1 column (loads and stores coalesced across the warp) and
+// writes Re(i^rot x) of the real field.
+template <typename T>
+__global__ void __launch_bounds__(256) k_fft_columns_re32(int f0, int nf, const c_t<T> *work, T *out,
+                                                          const int4 *terms, int nT) {
+    using C = c_t<T>;
+    constexpr int N = 32, NC = N * N;
+    const size_t gc = (size_t)blockIdx.x * 256 + threadIdx.x;
+    const int fl = (int)(gc / NC), c = (int)(gc % NC);
+    if (fl >= nf) return;
+    const C *in = work + (size_t)fl * N * NC + c;
+    C a[N];
+#pragma unroll
+    for (int r = 0; r < N; ++r) a[r] = in[(size_t)r * NC];
+    RegFFT<T, N>::run(a);
+    const int f = f0 + fl;
+    const int rot = terms ? terms[f % nT].w : 0;
+    T *o = out + (size_t)f * N * NC + c;
+#pragma unroll
+    for (int k = 0; k < N; ++k) o[(size_t)k * NC] = cipow(a[k], rot).x;
+}
+
 template <typename T>
 void fft_complex_realpart(const Geometry &g, const c_t<T> *in, int f0, int nf, c_t<T> *work, T *out,
                           const c_t<T> *const W[3], const int4 *terms, int nT, cudaStream_t s) {
     using C = c_t<T>;
+    if constexpr (sizeof(T) == 4) {
+        if (g.n[0] == 32 && g.n[1] == 32 && g.n[2] == 32) {
+            k_fft_planes_c32<T><<<(unsigned)((size_t)nf * 32 / C32_PP), 128, 0, s>>>(in, f0, work);
+            k_fft_columns_re32<T><<<(unsigned)(((size_t)nf * 1024 + 255) / 256), 256, 0, s>>>(f0, nf, work, out,
+                                                                                            terms, nT);
+            count_launches(2);
+            return;
+        }
+    }
     const size_t sm1 = (g.n[1] + g.n[2] + 2 * (size_t)g.n[1] * g.n[2]) * sizeof(C);
     if (sm1 > 48 * 1024)
         cudaFuncSetAttribute(k_fft_planes_c<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1);
