@@ -904,7 +904,7 @@ def run_rows(dev, cpu_rows=True):
 
 def run_profile_workload(name):
     """A small case of one row, run twice, for ncu captures (a few hundred MB on the device):
-    taylor = fcc 32^3, 321^3 voxels, P = 12; fft64 = the perovskite 64^3 model at P = 4 (175 fields
+    taylor = fcc 32^3, 321^3 voxels, P = 12 (taylor30: P = 30, 5456 monomials); fft64 = the perovskite 64^3 model at P = 4 (175 fields
     of 64^3), |hkl| <= 2; lanczos = occupancy 32^3 cells, 513^3 voxels,
     m = 2, m' = 8; subbox = the pyrochlore occupancy volume with n_sb = 5; subbox_dft = the
     random-origin displacive boxes on a 101 x 101 (h h l) plane; dw = the magnetic pyrochlore
@@ -915,12 +915,13 @@ def run_profile_workload(name):
     import paper_1809_07088_gb300 as ds
     import synthetic as syn
     ctx = ds.Context(0)
-    if name == "taylor":
+    if name in ("taylor", "taylor30"):
         m = syn.displacive_fcc(cells=(32, 32, 32), sigma=0.1, seed=5)
         m.qgrid = syn.symmetric_qgrid(5.0, m.cells)
         lm = ds.Model(ctx, m.lattice, m.sites, m.cells, 1, m.scat_len, m.ff_kind, m.ff_coef)
         lm.upload_displacements(np.ascontiguousarray(m.disp))
-        opts = dict(disorder=ds.DS_DISP, mode=ds.DS_TOTAL, precision=ds.DS_FP32, taylor_order=12)
+        opts = dict(disorder=ds.DS_DISP, mode=ds.DS_TOTAL, precision=ds.DS_FP32,
+                    taylor_order=12 if name == "taylor" else 30)
     elif name == "fft64":
         # the perovskite 64^3 model at Taylor order 4: 5 sites x 35 monomials = 175 fields of 64^3
         m = syn.perovskite_correlated()
@@ -1116,7 +1117,7 @@ def main():
     ap.add_argument("--serving", type=int, default=512, help="requests in the serving stream (0 = skip)")
     ap.add_argument("--no-rows", action="store_true", help="skip the per-row measurements")
     ap.add_argument("--no-graph", action="store_true", help="time direct calls instead of a replayed CUDA graph")
-    ap.add_argument("--profile-workload", choices=["taylor", "fft64", "lanczos", "subbox", "subbox_dft", "dw"], default=None,
+    ap.add_argument("--profile-workload", choices=["taylor", "taylor30", "fft64", "lanczos", "subbox", "subbox_dft", "dw"], default=None,
                     help="run one small row workload twice (for ncu captures) and exit")
     ap.add_argument("--streams", type=int, default=2, choices=[1, 2],
                     help="2: the two volumes of a step on two streams (their kernels overlap)")
