@@ -1012,8 +1012,10 @@ def _bucket(nsite):
     return min(SERVE_NSITE, key=lambda b: (abs(b - nsite), b))
 
 
-def _serve_stream(ds, ctx, pool, reqs, precision, rate_hz, seed):
-    """Replay `reqs` with Poisson arrivals at rate_hz; returns per-request latency / gpu ms."""
+def _serve_stream(ds, ctx, pool, reqs, precision, rate_hz, seed, svc=None):
+    """Replay `reqs` with Poisson arrivals at rate_hz; returns latency percentiles and, given the
+    service time of each request type alone (`svc`), the slowdown percentiles (latency / service
+    time: how much queueing and sharing stretched each request, independent of its size)."""
     import numpy as np
     import threading
     import torch
@@ -1039,7 +1041,7 @@ def _serve_stream(ds, ctx, pool, reqs, precision, rate_hz, seed):
                 opts.update(taylor_order=-1, taylor_eps=1e-6)
             tk = lm.submit((m.qgrid.h0, m.qgrid.step, m.qgrid.count), out, **opts)
             with cond:
-                pending.append((tk, out, m.qgrid.nvox))
+                pending.append((tk, out, m.qgrid.nvox, (r["n"], r["kind"], _bucket(r["nsite"]))))
                 cond.notify()
 
     th = threading.Thread(target=submitter)
@@ -1050,19 +1052,25 @@ def _serve_stream(ds, ctx, pool, reqs, precision, rate_hz, seed):
         with cond:
             while not pending:
                 cond.wait(1.0)
-            tk, out, nvox = pending.pop(0)
+            tk, out, nvox, key = pending.pop(0)
         info = ctx.wait(tk, 600.0)
-        results.append((info.latency_ms, info.gpu_ms, nvox))
+        results.append((info.latency_ms, info.gpu_ms, nvox, key))
         del out
         got += 1
     th.join()
     makespan = time.perf_counter() - t_start
     lat = np.array([r[0] for r in results])
     vox = sum(r[2] for r in results)
-    return {"requests": len(reqs), "rate_hz": rate_hz, "p50_ms": float(np.percentile(lat, 50)),
-            "p99_ms": float(np.percentile(lat, 99)), "mean_ms": float(lat.mean()),
-            "p99_over_p50": float(np.percentile(lat, 99) / np.percentile(lat, 50)),
-            "throughput": vox / makespan, "unit": UNIT, "makespan_s": makespan}
+    res = {"requests": len(reqs), "rate_hz": rate_hz, "p50_ms": float(np.percentile(lat, 50)),
+           "p99_ms": float(np.percentile(lat, 99)), "mean_ms": float(lat.mean()),
+           "p99_over_p50": float(np.percentile(lat, 99) / np.percentile(lat, 50)),
+           "throughput": vox / makespan, "unit": UNIT, "makespan_s": makespan}
+    if svc:
+        sd = np.array([r[0] / (1e3 * svc[r[3]]) for r in results])
+        res.update({"slowdown_p50": float(np.percentile(sd, 50)), "slowdown_p99": float(np.percentile(sd, 99)),
+                    "slowdown_p99_over_p50": float(np.percentile(sd, 99) / np.percentile(sd, 50)),
+                    "service_ms_min_max": [1e3 * min(svc.values()), 1e3 * max(svc.values())]})
+    return res
 
 
 def run_serving(nreq, nreq_fp64=32, seed=4):
@@ -1099,7 +1107,7 @@ def run_serving(nreq, nreq_fp64=32, seed=4):
             del o
         mean_svc = float(np.mean([svc[(r["n"], r["kind"], _bucket(r["nsite"]))] for r in sub]))
         rate = 0.7 / mean_svc
-        out["fp32" if precision == 1 else "fp64_plain"] = _serve_stream(ds, ctx, pool, sub, precision, rate, seed)
+        out["fp32" if precision == 1 else "fp64_plain"] = _serve_stream(ds, ctx, pool, sub, precision, rate, seed, svc)
         out["fp32" if precision == 1 else "fp64_plain"]["mean_service_ms"] = 1e3 * mean_svc
     for lm, _ in pool.values():
         lm.close()

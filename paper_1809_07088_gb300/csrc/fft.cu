@@ -450,6 +450,7 @@ __global__ void __launch_bounds__(256) k_fft_planes64(const FieldSource src, int
     constexpr int SR = 68;
     static_assert(N * SR * sizeof(T) <= N * PS * sizeof(C), "staging fits the plane buffer");
     T *stage = (T *)pl;
+#pragma unroll
     for (int c4 = tid; c4 < N * N / 4; c4 += 256) {
         const int cell = r1 * N * N + 4 * c4, g4 = cell >> 2;
         T x[4];
@@ -508,6 +509,7 @@ __global__ void __launch_bounds__(256) k_fft_planes64(const FieldSource src, int
     }
     __syncthreads();
     C *out = work + (size_t)blockIdx.x * (N * NH);
+#pragma unroll 4
     for (int i = tid; i < N * NH; i += 256) {
         const int k2 = i / NH, k3 = i - k2 * NH;
         out[i] = pl[k2 * PS + k3];
@@ -532,9 +534,19 @@ __global__ void __launch_bounds__(256) k_fft_columns64(const FieldSource src, in
     fft64_twiddles<T>(t, tw);
     const int fl = blockIdx.x / NCH, c0 = (blockIdx.x - fl * NCH) * CB, f = f0 + fl;
     const C *in = work + (size_t)fl * N * NCOL + c0;
-    for (int i = tid; i < N * CB; i += 256) {
-        const int r = i >> 5, c = i & (CB - 1);
-        cb[r * CS + c] = in[(size_t)r * NCOL + c];
+    {
+        // the block's 2048 values, eight loads in flight per thread
+        C x[N * CB / 256];
+#pragma unroll
+        for (int u = 0; u < N * CB / 256; ++u) {
+            const int i = tid + 256 * u, r = i >> 5, c = i & (CB - 1);
+            x[u] = in[(size_t)r * NCOL + c];
+        }
+#pragma unroll
+        for (int u = 0; u < N * CB / 256; ++u) {
+            const int i = tid + 256 * u, r = i >> 5, c = i & (CB - 1);
+            cb[r * CS + c] = x[u];
+        }
     }
     __syncthreads();
     C v[8];
@@ -547,6 +559,7 @@ __global__ void __launch_bounds__(256) k_fft_columns64(const FieldSource src, in
     int rot = 0;
     if (src.kind == SRC_DISP) rot = src.terms[(f % src.nf_per_model) % src.T].w;
     C *out = spec + (size_t)f * (N * NCOL) + c0;
+#pragma unroll
     for (int i = tid; i < N * CB; i += 256) {
         const int k1 = i >> 5, c = i & (CB - 1);
         out[(size_t)k1 * NCOL + c] = cipow(cb[k1 * CS + c], rot);
