@@ -36,6 +36,16 @@ __host__ __device__ __forceinline__ int fdivf(int a, int b) {
     return q;
 }
 
+// x / d for 0 <= x < 2^16 and 1 <= d < 2^15 as a multiply-high by m = ceil(2^32 / d): with
+// m d = 2^32 + e, 0 <= e < d, and x = q d + r, floor(x m / 2^32) = q + floor((r + x e / 2^32) / d) = q
+// because x e < 2^32 (d = 1 takes m = 0 and x itself)
+struct ItemDiv {
+    int d;
+    unsigned m;
+    __device__ __forceinline__ explicit ItemDiv(int dd) : d(dd), m(dd == 1 ? 0u : 0xFFFFFFFFu / (unsigned)dd + 1u) {}
+    __device__ __forceinline__ int div(int x) const { return m ? (int)__umulhi((unsigned)x, m) : x; }
+};
+
 struct AdjLayout {
     size_t gam, bv, W, pw, total;
 };
@@ -82,6 +92,7 @@ __global__ void __launch_bounds__(AS_THREADS, 512 / AS_THREADS)
         return;
     }
     const int nz1 = nz[0], nz2 = nz[1], nz3 = nz[2], ncol = nz2 * nz3, nzone = nz1 * ncol;
+    const ItemDiv dcol(ncol), dz3(nz3), dch((P + 1 + AS_CH - 1) / AS_CH);
     const AdjLayout L = adj_layout(P, zr);
     float2 *gam = (float2 *)(smem + L.gam);   // [h1][h2][h3]
     float2 *bv = (float2 *)(smem + L.bv);     // beta [h1][col], then V [(a, b)][h3]
@@ -153,7 +164,7 @@ __global__ void __launch_bounds__(AS_THREADS, 512 / AS_THREADS)
         // W[a][col] = sum_h1 x1(h1)^a beta(h1, col), four powers per item
         const int nch = (P1 + AS_CH - 1) / AS_CH;
         for (int it = tid; it < ncol * nch; it += AS_THREADS) {
-            const int col = it % ncol, a0 = (it / ncol) * AS_CH;
+            const int ch = dcol.div(it), col = it - ch * ncol, a0 = ch * AS_CH;
             float2 acc[AS_CH];
 #pragma unroll
             for (int q = 0; q < AS_CH; ++q) acc[q] = make_float2(0.f, 0.f);
@@ -171,7 +182,7 @@ __global__ void __launch_bounds__(AS_THREADS, 512 / AS_THREADS)
         __syncthreads();
         // V[(a, b)][h3] = sum_h2 x2(h2)^b W[a](h2, h3), b <= P - a, four powers per item
         for (int it = tid; it < P1 * nch * nz3; it += AS_THREADS) {
-            const int h3 = it % nz3, r = it / nz3, a = r / nch, b0 = (r - a * nch) * AS_CH;
+            const int r = dz3.div(it), h3 = it - r * nz3, a = dch.div(r), b0 = (r - a * nch) * AS_CH;
             if (b0 > P - a) continue;
             float2 acc[AS_CH];
 #pragma unroll
@@ -192,11 +203,14 @@ __global__ void __launch_bounds__(AS_THREADS, 512 / AS_THREADS)
         // Z[t(a, b, c)](k) = sum_h3 x3(h3)^c V[(a, b)](h3), c <= P - a - b, four powers per item
         float2 *Zs = Z + (((size_t)p.model * nsite + site) * nT) * ncell + k;
         for (int it = tid; it < nab * nch; it += AS_THREADS) {
-            const int ab = it / nch, c0 = (it - ab * nch) * AS_CH;
-            // (a, b) of pair index ab: a is the largest with a P1 - a (a - 1) / 2 <= ab
-            int a = 0;
-            while (a < P && (a + 1) * P1 - (a + 1) * a / 2 <= ab) ++a;
-            const int b = ab - (a * P1 - a * (a - 1) / 2);
+            const int ab = dch.div(it), c0 = (it - ab * nch) * AS_CH;
+            // (a, b) of pair index ab: a is the largest with ab0(a) = a (2 P1 - a + 1) / 2 <= ab, the
+            // smaller root of the quadratic (FP32 square root, one integer correction each way)
+            const float Bq = (float)(2 * P1 + 1);
+            int a = min((int)(0.5f * (Bq - sqrtf(fmaxf(0.f, Bq * Bq - 8.f * (float)ab)))), P);
+            if (a * (2 * P1 - a + 1) / 2 > ab) --a;
+            if (a < P && (a + 1) * (2 * P1 - a) / 2 <= ab) ++a;
+            const int b = ab - a * (2 * P1 - a + 1) / 2;
             const int lc = P - a - b;
             if (c0 > lc) continue;
             float2 acc[AS_CH];
@@ -209,10 +223,10 @@ __global__ void __launch_bounds__(AS_THREADS, 512 / AS_THREADS)
                 for (int q = 0; q < AS_CH; ++q)
                     if (c0 + q <= lc) acc[q] = __ffma2_rn(make_float2(pp[q], pp[q]), v, acc[q]);
             }
-            // monomial index of (a, b, c): lexicographic order, a outer, b middle, c inner
-            int t0 = 0;
-            for (int aa = 0; aa < a; ++aa) t0 += (P - aa + 1) * (P - aa + 2) / 2;
-            t0 += b * (P - a + 1) - b * (b - 1) / 2;
+            // monomial index of (a, b, c): lexicographic order, a outer, b middle, c inner; the
+            // monomials with a' < a number T(P) - T(P - a)
+            const int t0 = (P1 * (P1 + 1) * (P1 + 2) - (P1 - a) * (P1 - a + 1) * (P1 - a + 2)) / 6 +
+                           b * (P - a + 1) - b * (b - 1) / 2;
 #pragma unroll
             for (int q = 0; q < AS_CH; ++q)
                 if (c0 + q <= lc) Zs[(size_t)(t0 + c0 + q) * ncell] = acc[q];
