@@ -28,7 +28,7 @@ namespace {
 
 constexpr int AS_ZR = 17;        // zones per axis handled (at most)
 constexpr int AS_PMAX = 31;      // Taylor order handled
-constexpr int AS_CH = 4;         // powers per thread item
+constexpr int AS_CH = 4;         // powers per thread item (one 16-byte load of the power table)
 
 __host__ __device__ __forceinline__ int fdivf(int a, int b) {
     int q = a / b;
@@ -57,7 +57,7 @@ __host__ __device__ __forceinline__ AdjLayout adj_layout(int P, int zr) {
     L.bv = al(L.gam + z3 * sizeof(float2));
     L.W = al(L.bv + std::max(z3, nab * zr) * sizeof(float2));
     L.pw = al(L.W + (size_t)(P + 1) * zr * zr * sizeof(float2));
-    L.total = al(L.pw + (size_t)3 * zr * (P + 1) * sizeof(float));
+    L.total = al(L.pw + (size_t)3 * zr * ((P + 1 + 3) & ~3) * sizeof(float));   // rows padded to 4
     return L;
 }
 
@@ -80,7 +80,7 @@ __global__ void __launch_bounds__(AS_THREADS, 512 / AS_THREADS)
         const int hi = fdivf(gm.g0[a] + gm.cnt[a] - 1 - kk[a], g.n[a]);
         nz[a] = max(0, hi - lo[a] + 1);
     }
-    const int nsite = p.nsite, nT = p.nT, P1 = P + 1;
+    const int nsite = p.nsite, nT = p.nT, P1 = P + 1, P1p = (P1 + 3) & ~3;   // power rows padded to 4
     const int tid = threadIdx.x;
     const size_t ncell = g.ncell;
     if (nz[0] * nz[1] * nz[2] == 0) {
@@ -105,9 +105,10 @@ __global__ void __launch_bounds__(AS_THREADS, 512 / AS_THREADS)
         const double x = ((double)(lo[a] + j) + (double)kk[a] / g.n[a]) / p.gscale[a];
         double v = 1.0;
         for (int e = 0; e <= P; ++e) {
-            pw[(size_t)i * P1 + e] = j < nz[a] ? (float)v : 0.f;
+            pw[(size_t)i * P1p + e] = j < nz[a] ? (float)v : 0.f;
             v *= x;
         }
+        for (int e = P1; e < P1p; ++e) pw[(size_t)i * P1p + e] = 0.f;
     }
     // gamma = scale dL/dI conj(F) of the model, per zone of the box
     const size_t nv = (size_t)gm.cnt[0] * gm.cnt[1] * gm.cnt[2];
@@ -170,7 +171,8 @@ __global__ void __launch_bounds__(AS_THREADS, 512 / AS_THREADS)
             for (int q = 0; q < AS_CH; ++q) acc[q] = make_float2(0.f, 0.f);
             for (int h1 = 0; h1 < nz1; ++h1) {
                 const float2 b = bv[h1 * ncol + col];
-                const float *pp = pw + (size_t)(0 * zr + h1) * P1 + a0;
+                const float4 p4 = *(const float4 *)(pw + (size_t)(0 * zr + h1) * P1p + a0);
+                const float pp[AS_CH] = {p4.x, p4.y, p4.z, p4.w};
 #pragma unroll
                 for (int q = 0; q < AS_CH; ++q)
                     if (a0 + q < P1) acc[q] = __ffma2_rn(make_float2(pp[q], pp[q]), b, acc[q]);
@@ -189,7 +191,8 @@ __global__ void __launch_bounds__(AS_THREADS, 512 / AS_THREADS)
             for (int q = 0; q < AS_CH; ++q) acc[q] = make_float2(0.f, 0.f);
             for (int h2 = 0; h2 < nz2; ++h2) {
                 const float2 w = W[(size_t)a * ncol + h2 * nz3 + h3];
-                const float *pp = pw + (size_t)(1 * zr + h2) * P1 + b0;
+                const float4 p4 = *(const float4 *)(pw + (size_t)(1 * zr + h2) * P1p + b0);
+                const float pp[AS_CH] = {p4.x, p4.y, p4.z, p4.w};
 #pragma unroll
                 for (int q = 0; q < AS_CH; ++q)
                     if (b0 + q <= P - a) acc[q] = __ffma2_rn(make_float2(pp[q], pp[q]), w, acc[q]);
@@ -218,7 +221,8 @@ __global__ void __launch_bounds__(AS_THREADS, 512 / AS_THREADS)
             for (int q = 0; q < AS_CH; ++q) acc[q] = make_float2(0.f, 0.f);
             for (int h3 = 0; h3 < nz3; ++h3) {
                 const float2 v = bv[(size_t)ab * nz3 + h3];
-                const float *pp = pw + (size_t)(2 * zr + h3) * P1 + c0;
+                const float4 p4 = *(const float4 *)(pw + (size_t)(2 * zr + h3) * P1p + c0);
+                const float pp[AS_CH] = {p4.x, p4.y, p4.z, p4.w};
 #pragma unroll
                 for (int q = 0; q < AS_CH; ++q)
                     if (c0 + q <= lc) acc[q] = __ffma2_rn(make_float2(pp[q], pp[q]), v, acc[q]);

@@ -206,7 +206,7 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_taylor_sf(const __grid_constan
         const C *spec_s = p.spec + ((size_t)(p.model * nsite + site) * p.nT) * nh + kidx;
         for (int gi = pl.ngroups - 1; gi >= 0; --gi) {
             const int a0 = pl.a0[gi], a1 = pl.a0[gi + 1];
-            // step 1: X[h3][xi(a, b)] = sum_c M'_abc x3^c, one (a, b) chain per slot
+            // step 1: X[xi(a, b)][h3] = sum_c M'_abc x3^c, one (a, b) chain per slot
             for (int slot = pl.ibeg[gi] + tid; slot < pl.ibeg[gi + 1]; slot += NT) {
                 const int4 it = pl.items[slot];
                 if (it.x < 0) continue;
@@ -234,7 +234,7 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_taylor_sf(const __grid_constan
                 }
 #pragma unroll
                 for (int j = 0; j < ZR; ++j)
-                    if (j < nz3) Xs[j * pl.xpad + it.w] = acc[j];
+                    Xs[it.w * ZR + j] = acc[j];   // [item][h3], rows of ZR (odd): distinct banks
             }
             __syncthreads();
             // step 2: Y[al][h2][h3] = sum_b X[h3][xi(a, b)] x2^b, one (a, h3) per item
@@ -245,13 +245,13 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_taylor_sf(const __grid_constan
                 T x2[ZR];
 #pragma unroll
                 for (int j = 0; j < ZR; ++j) x2[j] = xs[ZR + j];
-                const C *xr = Xs + (size_t)h3 * pl.xpad + sf_xi(P, a0, a, 0);
+                const C *xr = Xs + (size_t)sf_xi(P, a0, a, 0) * ZR + h3;
                 C acc[ZR];
-                const C top = xr[Lb - 1];
+                const C top = xr[(Lb - 1) * ZR];
 #pragma unroll
                 for (int j = 0; j < ZR; ++j) acc[j] = top;
                 for (int b = Lb - 2; b >= 0; --b) {
-                    const C v = xr[b];
+                    const C v = xr[b * ZR];
 #pragma unroll
                     for (int j = 0; j < ZR; ++j) acc[j] = hfma(acc[j], x2[j], v);
                 }
