@@ -1030,19 +1030,34 @@ __global__ void k_avg0(int nmodels, int nsite, int nT, int ncell_h, const int4 *
     avg0[idx] = cscale(acc, T(1) / T(nmodels));
 }
 
+// <F(H)> per zone H (Eq. bragg_sf_disp with the Taylor series of <exp(iQ.u)>): a warp per zone.
+// Lane 0 tabulates the zone's powers x_a^e (e <= P) of the scaled coefficient variables in shared
+// memory; the lanes split each site's monomials, x1^a x2^b x3^c times the site's mean coefficient,
+// and a warp reduction gives the site sum; phases and the class form factors as in Eq. sf.
 template <typename T>
-__global__ void k_bragg_disp(RecombParams<T> p, const c_t<T> *avg0, c_t<T> *bragg_out) {
+__global__ void __launch_bounds__(256) k_bragg_disp(RecombParams<T> p, const c_t<T> *avg0, c_t<T> *bragg_out, int P) {
     using C = c_t<T>;
+    extern __shared__ double bragg_pw[];
     const GridMap &gm = p.gm;
     const int nz = gm.nH[0] * gm.nH[1] * gm.nH[2];
-    const int z = blockIdx.x * blockDim.x + threadIdx.x;
-    if (z >= nz) return;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int z = blockIdx.x * 8 + warp;
+    if (z >= nz) return;   // whole warps only: no block-wide barrier below
+    const int P1 = P + 1;
+    double *pw = bragg_pw + warp * 3 * P1;
     const int h3 = z % gm.nH[2], h2 = (z / gm.nH[2]) % gm.nH[1], h1 = z / (gm.nH[2] * gm.nH[1]);
     const int G1 = p.g.n[0] * (gm.Hmin[0] + h1), G2 = p.g.n[1] * (gm.Hmin[1] + h2), G3 = p.g.n[2] * (gm.Hmin[2] + h3);
     double Qd[3], Xd[3];
     q_of_G(p.recip, p.g.n, G1, G2, G3, Qd);
     x_of_G(p.gscale, p.g.n, G1, G2, G3, Xd);
-    const double qx = Xd[0], qy = Xd[1], qz = Xd[2];
+    if (lane < 3) {
+        double v = 1.0;
+        for (int e = 0; e <= P; ++e) {
+            pw[lane * P1 + e] = v;
+            v *= Xd[lane];
+        }
+    }
+    __syncwarp();
     const T q2 = (T)(Qd[0] * Qd[0] + Qd[1] * Qd[1] + Qd[2] * Qd[2]);
     const T s2 = q2 * (T)(1.0 / (FOUR_PI_D * FOUR_PI_D));
     C F = mk<T>(T(0), T(0)), part = mk<T>(T(0), T(0));
@@ -1050,19 +1065,21 @@ __global__ void k_bragg_disp(RecombParams<T> p, const c_t<T> *avg0, c_t<T> *brag
     const int pz = p.pzone ? p.pzone[z] : 1 << 30;  // the zone's Taylor order
     for (int s = 0; s < p.nsite; ++s) {
         const int site = p.site_of[s];
-        double ca = 1, cb = 1, cc = 1;
-        C S = mk<T>(T(0), T(0));
-        for (int t = 0; t < p.nT; ++t) {
-            const int op = p.ops[t];
-            if (op == OP_MULZ) cc *= qz;
-            else if (op == OP_NEWB) { cb *= qy; cc = cb; }
-            else if (op == OP_NEWA) { ca *= qx; cb = ca; cc = ca; }
-            else { ca = cb = cc = 1; }
-            if (p.terms[t].w > pz) continue;
+        T sx = T(0), sy = T(0);
+        for (int t = lane; t < p.nT; t += 32) {
+            const int4 tm = p.terms[t];
+            if (tm.w > pz) continue;
+            const T mono = (T)(pw[tm.x] * pw[P1 + tm.y] * pw[2 * P1 + tm.z]);
             const C m = avg0[(size_t)site * p.nT + t];
-            S.x += (T)cc * m.x;
-            S.y += (T)cc * m.y;
+            sx = fma(mono, m.x, sx);
+            sy = fma(mono, m.y, sy);
         }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            sx += __shfl_xor_sync(0xffffffffu, sx, o);
+            sy += __shfl_xor_sync(0xffffffffu, sy, o);
+        }
+        const C S = mk<T>(sx, sy);
         const C *tH = p.phH + (size_t)site * 3 * p.nHmax;
         C ph = cmul(cmul(tH[h1], tH[p.nHmax + h2]), tH[2 * p.nHmax + h3]);
         ph = cscale(ph, p.scat[site]);
@@ -1074,7 +1091,7 @@ __global__ void k_bragg_disp(RecombParams<T> p, const c_t<T> *avg0, c_t<T> *brag
             ++cls;
         }
     }
-    bragg_out[z] = F;
+    if (lane == 0) bragg_out[z] = F;
 }
 
 template <typename T>
@@ -1082,7 +1099,11 @@ void displacive_bragg(const RecombParams<T> &p, const int4 *terms, c_t<T> *avg0,
     const int n0 = p.nsite * p.nT;
     k_avg0<T><<<(n0 + 255) / 256, 256, 0, s>>>(p.nmodels, p.nsite, p.nT, p.g.ncell_h, terms, p.spec, avg0);
     const int nz = p.gm.nH[0] * p.gm.nH[1] * p.gm.nH[2];
-    k_bragg_disp<T><<<(nz + 127) / 128, 128, 0, s>>>(p, avg0, bragg);
+    int P = 0;   // the order of the nT monomials: (P + 1)(P + 2)(P + 3) / 6 = nT
+    while ((P + 1) * (P + 2) * (P + 3) / 6 < p.nT) ++P;
+    const size_t sm = (size_t)8 * 3 * (P + 1) * sizeof(double);
+    if (sm > 48 * 1024) cudaFuncSetAttribute(k_bragg_disp<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_bragg_disp<T><<<(nz + 7) / 8, 256, sm, s>>>(p, avg0, bragg, P);
     count_launches(2);
 }
 
