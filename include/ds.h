@@ -172,8 +172,10 @@ ds_status ds_request_intensity(ds_model *model, const ds_qgrid *grid, const ds_o
  * opts->smoothing must be DS_SMOOTH_LANCZOS or DS_SMOOTH_SPHERE, with lanczos_m and lanczos_mprime): the sum runs
  * over floor(Q_a) - M + 1 <= G_a <= floor(Q_a) + M, M = ceil(m m'/2), inside the strict window
  * |Q_a - G_a| < m m'/2 (Q_a = n_a h_a).  I(G) is computed by the FFT method on the box of Bragg
- * positions that covers every point's support.  The call returns when the values are written
- * (it synchronises `stream`).  Errors: DS_ERR_ARG (smoothing, non-finite points), DS_ERR_ADMISSION
+ * positions that covers every point's support.  The points are scaled and bounded on the device;
+ * the call synchronises `stream` once to read their bounds back (a few KB).  With out_is_device
+ * the rest is queued on `stream` and the call returns without waiting; with a host `out` it
+ * returns when the values are copied.  Errors: DS_ERR_ARG (smoothing, non-finite points), DS_ERR_ADMISSION
  * (box larger than the budget), DS_ERR_UNSUPPORTED, the errors of ds_request_intensity. */
 ds_status ds_request_points(ds_model *model, const double *hkl, int64_t npts, int hkl_is_device, const ds_opts *opts,
                             void *out, int out_is_device, void *stream, ds_result_info *info);

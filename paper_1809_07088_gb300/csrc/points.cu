@@ -141,34 +141,70 @@ void launch_points(const T *vol, const int box[3], const int cnt[3], const doubl
     count_launches(1);
 }
 
+// Q_a = n_a h_a (supercell-index units) written to Q, and per block the range of floor(Q_a) over
+// the finite points and the index of the first non-finite one (slots lo[3], hi[3], bad).  hkl and
+// Q may be the same buffer: each element is read and written by one thread.
+constexpr int PB_THREADS = 256;
+constexpr int PB_SLOTS = 7;
+
+__global__ void __launch_bounds__(PB_THREADS)
+    k_points_scale(const double *hkl, long long npts, double n0, double n1, double n2, double *Q, double *part) {
+    const double n[3] = {n0, n1, n2};
+    double v[PB_SLOTS] = {INFINITY, INFINITY, INFINITY, -INFINITY, -INFINITY, -INFINITY, INFINITY};
+    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < npts;
+         p += (long long)gridDim.x * blockDim.x) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const double q = hkl[3 * p + a] * n[a];
+            Q[3 * p + a] = q;
+            if (!isfinite(q)) {
+                v[6] = fmin(v[6], (double)p);
+            } else {
+                const double f = floor(q);
+                v[a] = fmin(v[a], f);
+                v[3 + a] = fmax(v[3 + a], f);
+            }
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int s = 0; s < PB_SLOTS; ++s) {
+            const double w = __shfl_xor_sync(0xffffffffu, v[s], o);
+            v[s] = (s >= 3 && s < 6) ? fmax(v[s], w) : fmin(v[s], w);
+        }
+    __shared__ double red[PB_THREADS / 32][PB_SLOTS];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0)
+#pragma unroll
+        for (int s = 0; s < PB_SLOTS; ++s) red[wid][s] = v[s];
+    __syncthreads();
+    if (threadIdx.x < PB_SLOTS) {
+        const int s = threadIdx.x;
+        double r = red[0][s];
+        for (int w = 1; w < PB_THREADS / 32; ++w) r = (s >= 3 && s < 6) ? fmax(r, red[w][s]) : fmin(r, red[w][s]);
+        part[(size_t)blockIdx.x * PB_SLOTS + s] = r;
+    }
+}
+
+// dQ: the points in supercell-index units on the device; fl_lo/fl_hi: the range of floor(Q_a)
 template <typename T>
-ds_status run_points(ds_model *Mdl, const std::vector<double> &Qh, long long npts, const ds_opts *o, void *out,
-                     int out_dev, cudaStream_t st, ds_result_info *info) {
+ds_status run_points(ds_model *Mdl, const double *dQ, const double fl_lo[3], const double fl_hi[3], long long npts,
+                     const ds_opts *o, void *out, int out_dev, cudaStream_t st, Scratch &ws, ds_result_info *info) {
     ds_ctx *ctx = Mdl->ctx;
     const int m = o->lanczos_m, mp = o->lanczos_mprime;
     const double rcut = (1.0 - 1.0 / m) / mp, meff = 0.5 * m * mp;
     const int M = (int)std::ceil(meff);
-    // box of Bragg positions covering every point's support
-    long long lo[3], hi[3];
-    for (int a = 0; a < 3; ++a) {
-        lo[a] = LLONG_MAX;
-        hi[a] = LLONG_MIN;
-    }
-    for (long long p = 0; p < npts; ++p)
-        for (int a = 0; a < 3; ++a) {
-            const long long f = (long long)std::floor(Qh[3 * p + a]);
-            lo[a] = std::min(lo[a], f - M + 1);
-            hi[a] = std::max(hi[a], f + M);
-        }
+    // box of Bragg positions covering every point's support: floor(Q_a) - M + 1 .. floor(Q_a) + M
     ds_qgrid box;
     int b[3], cnt[3];
     size_t nvox = 1;
     for (int a = 0; a < 3; ++a) {
-        if (hi[a] - lo[a] + 1 > (1 << 20) || std::llabs(lo[a]) > 100000000LL)
+        if (!(std::fabs(fl_lo[a]) <= 1e8 && std::fabs(fl_hi[a]) <= 1e8) || fl_hi[a] - fl_lo[a] + 2 * M > (1 << 20))
             return ds_fail(ctx, DS_ERR_UNSUPPORTED, "points span too many Bragg positions along axis %d", a);
-        b[a] = (int)lo[a];
-        cnt[a] = (int)(hi[a] - lo[a] + 1);
-        box.h0[a] = (double)lo[a] / Mdl->n[a];
+        b[a] = (int)fl_lo[a] - M + 1;
+        cnt[a] = (int)(fl_hi[a] - fl_lo[a]) + 2 * M;
+        box.h0[a] = (double)b[a] / Mdl->n[a];
         box.step[a] = 1.0 / Mdl->n[a];
         box.count[a] = cnt[a];
         nvox *= (size_t)cnt[a];
@@ -178,15 +214,11 @@ ds_status run_points(ds_model *Mdl, const std::vector<double> &Qh, long long npt
                        nvox * sizeof(T), ctx->budget);
     ds_opts ob = *o;
     ob.smoothing = DS_SMOOTH_NONE;
-    Scratch ws(st);
     T *vol = (T *)ws.get(sizeof(T) * nvox);
-    double *dQ = (double *)ws.get(sizeof(double) * 3 * npts);
     T *dout = out_dev ? (T *)out : (T *)ws.get(sizeof(T) * npts);
     if (ws.failed) return ds_fail(ctx, DS_ERR_OOM, "device allocation failed (points)");
     ds_status rc = plan_and_run<T>(Mdl, &box, &ob, vol, st, ws, info, nullptr);
     if (rc != DS_OK) return rc;
-    if (cudaMemcpyAsync(dQ, Qh.data(), sizeof(double) * 3 * npts, cudaMemcpyHostToDevice, st) != cudaSuccess)
-        return ds_fail(ctx, DS_ERR_CUDA, "copy of the points failed");
     if (o->smoothing == DS_SMOOTH_SPHERE) {
         ProfScope ps(ctx, "lanczos_points", st);
         SphereGeom sg;
@@ -199,11 +231,12 @@ ds_status run_points(ds_model *Mdl, const std::vector<double> &Qh, long long npt
         ProfScope ps(ctx, "lanczos_points", st);
         launch_points<T>(vol, b, cnt, dQ, npts, M, rcut, meff, dout, st);
     }
+    if (cudaGetLastError() != cudaSuccess) return ds_fail(ctx, DS_ERR_CUDA, "points launch failed");
     if (!out_dev && cudaMemcpyAsync(out, dout, sizeof(T) * npts, cudaMemcpyDeviceToHost, st) != cudaSuccess)
         return ds_fail(ctx, DS_ERR_CUDA, "copy of the intensities to the host failed");
     ws.release();
-    // the host copy of the points must outlive the copy queued above; host outputs are waited for
-    if (cudaStreamSynchronize(st) != cudaSuccess)
+    // a host output is complete on return; a device output is ordered on the stream
+    if (!out_dev && cudaStreamSynchronize(st) != cudaSuccess)
         return ds_fail(ctx, DS_ERR_CUDA, "stream synchronisation failed: %s", cudaGetErrorString(cudaGetLastError()));
     if (info) info->nvox = npts;
     return DS_OK;
@@ -226,28 +259,45 @@ extern "C" ds_status ds_request_points(ds_model *Mdl, const double *hkl, int64_t
     if (npts == 0) return DS_OK;
     if (cudaSetDevice(ctx->device) != cudaSuccess) return ds_fail(ctx, DS_ERR_CUDA, "cudaSetDevice");
     cudaStream_t st = (cudaStream_t)stream;
-    std::vector<double> Qh((size_t)npts * 3);
-    if (hkl_is_device) {
-        if (cudaMemcpy(Qh.data(), hkl, sizeof(double) * 3 * npts, cudaMemcpyDeviceToHost) != cudaSuccess)
-            return ds_fail(ctx, DS_ERR_CUDA, "copy of the points to the host failed");
-    } else {
-        std::copy(hkl, hkl + 3 * npts, Qh.begin());
-    }
-    for (long long p = 0; p < npts; ++p)
-        for (int a = 0; a < 3; ++a) {
-            const double q = Qh[3 * p + a] * Mdl->n[a];  // supercell-index units, Q_a = n_a h_a
-            if (!std::isfinite(q)) return ds_fail(ctx, DS_ERR_ARG, "point %lld is not finite", p);
-            Qh[3 * p + a] = q;
-        }
-    // options and model state, checked on a one-voxel grid at the first point's floor
+    // options and model state, checked on a one-voxel grid at the origin before any work is queued
     ds_qgrid probe;
     for (int a = 0; a < 3; ++a) {
-        probe.h0[a] = std::floor(Qh[a]) / Mdl->n[a];
+        probe.h0[a] = 0.0;
         probe.step[a] = 1.0 / Mdl->n[a];
         probe.count[a] = 1;
     }
     ds_status rc = check_request(Mdl, &probe, o);
     if (rc != DS_OK) return rc;
-    if (o->precision == DS_FP64) return run_points<double>(Mdl, Qh, npts, o, out, out_is_device, st, info);
-    return run_points<float>(Mdl, Qh, npts, o, out, out_is_device, st, info);
+    // the points scaled to Q_a = n_a h_a on the device; only their per-block bounds come back
+    Scratch ws(st);
+    const unsigned nb = (unsigned)std::max<long long>(1, std::min<long long>((npts + PB_THREADS - 1) / PB_THREADS, 152 * 2));
+    double *dQ = (double *)ws.get(sizeof(double) * 3 * npts);
+    double *dpart = (double *)ws.get(sizeof(double) * PB_SLOTS * nb);
+    if (ws.failed) return ds_fail(ctx, DS_ERR_OOM, "device allocation failed (points)");
+    if (!hkl_is_device && cudaMemcpyAsync(dQ, hkl, sizeof(double) * 3 * npts, cudaMemcpyHostToDevice, st) != cudaSuccess)
+        return ds_fail(ctx, DS_ERR_CUDA, "copy of the points failed");
+    k_points_scale<<<nb, PB_THREADS, 0, st>>>(hkl_is_device ? hkl : dQ, npts, (double)Mdl->n[0], (double)Mdl->n[1],
+                                             (double)Mdl->n[2], dQ, dpart);
+    count_launches(1);
+    if (cudaGetLastError() != cudaSuccess) return ds_fail(ctx, DS_ERR_CUDA, "points launch failed");
+    std::vector<double> part((size_t)PB_SLOTS * nb);
+    if (cudaMemcpyAsync(part.data(), dpart, sizeof(double) * part.size(), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return ds_fail(ctx, DS_ERR_CUDA, "read-back of the point bounds failed: %s", cudaGetErrorString(cudaGetLastError()));
+    double lo[3], hi[3], bad = INFINITY;
+    for (int a = 0; a < 3; ++a) {
+        lo[a] = INFINITY;
+        hi[a] = -INFINITY;
+    }
+    for (unsigned k = 0; k < nb; ++k) {
+        const double *v = part.data() + (size_t)k * PB_SLOTS;
+        for (int a = 0; a < 3; ++a) {
+            lo[a] = std::min(lo[a], v[a]);
+            hi[a] = std::max(hi[a], v[3 + a]);
+        }
+        bad = std::min(bad, v[6]);
+    }
+    if (bad < INFINITY) return ds_fail(ctx, DS_ERR_ARG, "point %lld is not finite", (long long)bad);
+    if (o->precision == DS_FP64) return run_points<double>(Mdl, dQ, lo, hi, npts, o, out, out_is_device, st, ws, info);
+    return run_points<float>(Mdl, dQ, lo, hi, npts, o, out, out_is_device, st, ws, info);
 }
