@@ -13,6 +13,7 @@
 // window (one read, one write): HBM bound, about 16 bytes per FP32 voxel.  Wider stencils take one
 // thread per output and one pass per axis.
 #include <algorithm>
+#include <cstdint>
 
 #include "internal.h"
 #include "noise.h"
@@ -135,6 +136,13 @@ __global__ void __launch_bounds__(256) k_lanczos_mid(const T *__restrict__ in, T
 // the axis-B stencil gives one output row per input row.  The row loop is unrolled by D, a
 // multiple of NT, so both rings are indexed by constants.
 template <int NT> constexpr int plane_depth() { return NT * ((8 + NT - 1) / NT); }
+// width of a ring slot of the in-plane kernel: a row's 2 nthr + NT - 1 staged inputs after its
+// shift (< E elements) from a 16-byte boundary, one more value for the paired loads of an odd
+// shift, rounded up to whole 16-byte chunks
+template <typename T, int NT> __host__ __device__ constexpr int plane_slot(int nthr) {
+    constexpr int E = 16 / sizeof(T);
+    return (2 * nthr + NT + 1 + E - 1 + E - 1) / E * E;
+}
 template <typename T, int NT>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 3) k_lanczos_plane(const T *__restrict__ in, T *__restrict__ out, int A, int B,
                                                        int C, int L, const __grid_constant__ Taps<T> tp) {
@@ -142,7 +150,8 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 3) k_lanczos_plane(c
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *buf = (T *)smem_raw;
     const int tid = threadIdx.x, nthr = blockDim.x;
-    const int W = 2 * nthr, SW = W + NT + 1;   // staged width of a row (even: 8- and 16-byte loads)
+    constexpr int E = 16 / sizeof(T);            // elements per 16-byte copy
+    const int W = 2 * nthr, SW = plane_slot<T, NT>(nthr);
     const int Bo = B - (NT - 1), Co = C - (NT - 1);
     const int nrun = (Bo + L - 1) / L;
     const int a = blockIdx.y / nrun, run = blockIdx.y - a * nrun;
@@ -153,12 +162,24 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 3) k_lanczos_plane(c
     T *dst = out + ((size_t)a * Bo + b0) * Co + c0 + 2 * tid;
     const bool act0 = c0 + 2 * tid < Co, act1 = c0 + 2 * tid + 1 < Co;
     const int nrow = b1 - b0 + NT - 1;
-    // row i of the run into buffer `slot` (one commit group per row, empty past the run)
+    // offset of row i's first element from a 16-byte boundary, in elements: the row is staged at
+    // that offset in its slot, so a 16-byte chunk of the row lands on a 16-byte boundary
+    auto shift = [&](int i) { return (int)(((uintptr_t)(src + (size_t)i * C) / sizeof(T)) % E); };
+    // row i of the run into buffer `slot` (one commit group per row, empty past the run): whole
+    // 16-byte chunks, and element copies for the at most 2 (E - 1) values before the first and
+    // after the last chunk
     auto issue = [&](int i, int slot) {
         if (i < nrow) {
             const T *row = src + (size_t)i * C;
-            T *sb = buf + slot * SW;
-            for (int j = tid; j < nw; j += nthr) cp_async<sizeof(T)>(sb + j, row + j);
+            const int m = shift(i);
+            T *sb = buf + slot * SW + m;
+            const int ja = min((E - m) % E, nw), nb = (nw - ja) / E, jt = ja + nb * E;
+            for (int c = tid; c < nb; c += nthr) cp_async<16>(sb + ja + c * E, row + ja + c * E);
+            const int ne = ja + (nw - jt);
+            for (int e = tid; e < ne; e += nthr) {
+                const int j = e < ja ? e : jt + (e - ja);
+                cp_async<sizeof(T)>(sb + j, row + j);
+            }
         }
         cp_async_commit();
     };
@@ -175,16 +196,29 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 3) k_lanczos_plane(c
             cp_async_wait<D - 2>();   // row i has landed (this thread's copies)
             __syncthreads();          // every thread's copies of row i; row i - 1 is no longer read
             issue(i + D - 1, (u + D - 1) % D);
-            const T *sb = buf + u * SW + 2 * tid;
+            const int m = shift(i);
+            const T *sb = buf + u * SW + m + 2 * tid;
             T v[NT + 1];
+            if constexpr (sizeof(T) == 4) {
+                // 8-byte loads from an even offset: the row's own for an even shift, one value
+                // earlier for an odd one (uniform over the CTA)
+                if ((m & 1) == 0) {
 #pragma unroll
-            for (int q = 0; q < (NT + 1) / 2; ++q) {
-                if constexpr (sizeof(T) == 4) {
-                    const float2 p2 = ((const float2 *)sb)[q];
-                    v[2 * q] = p2.x, v[2 * q + 1] = p2.y;
+                    for (int q = 0; q < (NT + 1) / 2; ++q) {
+                        const float2 p2 = ((const float2 *)sb)[q];
+                        v[2 * q] = p2.x, v[2 * q + 1] = p2.y;
+                    }
                 } else {
-                    v[2 * q] = sb[2 * q], v[2 * q + 1] = sb[2 * q + 1];
+#pragma unroll
+                    for (int q = 0; q < (NT + 3) / 2; ++q) {
+                        const float2 p2 = ((const float2 *)(sb - 1))[q];
+                        if (q > 0 && 2 * q - 1 <= NT) v[2 * q - 1] = p2.x;
+                        if (2 * q <= NT) v[2 * q] = p2.y;
+                    }
                 }
+            } else {
+#pragma unroll
+                for (int t = 0; t <= NT; ++t) v[t] = sb[t];
             }
             T x0 = T(0), x1 = T(0);
 #pragma unroll
@@ -231,7 +265,7 @@ static void sliding_passes(const T *ext, T *tmp1, T *tmp2, T *out, int d[3], con
         const int nthr = 32 * ((per + 63) / 64);
         const int L = run_len(nseg, d[0], Bo);
         const int nrun = (Bo + L - 1) / L;
-        const size_t sm = (size_t)plane_depth<NT>() * (2 * nthr + NT + 1) * sizeof(T);
+        const size_t sm = (size_t)plane_depth<NT>() * plane_slot<T, NT>(nthr) * sizeof(T);
         if (sm > 48 * 1024) cudaFuncSetAttribute(k_lanczos_plane<T, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         dim3 grid((unsigned)((Co + 2 * nthr - 1) / (2 * nthr)), (unsigned)(d[0] * nrun));
         k_lanczos_plane<T, NT><<<grid, nthr, sm, s>>>(ext, tmp1, d[0], d[1], d[2], L, tp);
