@@ -14,6 +14,7 @@
 // thread per output and one pass per axis.
 #include <algorithm>
 #include <cstdint>
+#include <type_traits>
 
 #include "internal.h"
 #include "noise.h"
@@ -185,9 +186,12 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 3) k_lanczos_plane(c
     };
 #pragma unroll
     for (int u = 0; u < D - 1; ++u) issue(u, u);
-    T r0[NT], r1[NT];   // the last NT axis-C values of the two columns (slot = row mod NT)
+    // the last NT axis-C values of the two columns (slot = row mod NT), as one pair per row: the
+    // axis-B stencil of both columns runs on pairs (FFMA2 in FP32)
+    using P2 = typename std::conditional<sizeof(T) == 4, float2, double2>::type;
+    P2 r[NT];
 #pragma unroll
-    for (int t = 0; t < NT; ++t) r0[t] = r1[t] = T(0);
+    for (int t = 0; t < NT; ++t) r[t].x = r[t].y = T(0);
     for (int i0 = 0; i0 < nrow; i0 += D) {
 #pragma unroll
         for (int u = 0; u < D; ++u) {
@@ -223,19 +227,24 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 3) k_lanczos_plane(c
             T x0 = T(0), x1 = T(0);
 #pragma unroll
             for (int t = 0; t < NT; ++t) x0 = fma(tp.w[t], v[t], x0), x1 = fma(tp.w[t], v[t + 1], x1);
-            r0[u % NT] = x0;
-            r1[u % NT] = x1;
+            r[u % NT].x = x0;
+            r[u % NT].y = x1;
             if (i >= NT - 1) {
-                T y0 = T(0), y1 = T(0);
+                P2 y;
+                y.x = y.y = T(0);
 #pragma unroll
                 for (int t = 0; t < NT; ++t) {
                     const int sl = (u + 1 + t) % NT;   // row i - NT + 1 + t, oldest first
-                    y0 = fma(tp.w[t], r0[sl], y0);
-                    y1 = fma(tp.w[t], r1[sl], y1);
+                    if constexpr (sizeof(T) == 4) {
+                        y = __ffma2_rn(make_float2(tp.w[t], tp.w[t]), r[sl], y);
+                    } else {
+                        y.x = fma(tp.w[t], r[sl].x, y.x);
+                        y.y = fma(tp.w[t], r[sl].y, y.y);
+                    }
                 }
                 T *o = dst + (size_t)(i - (NT - 1)) * Co;
-                if (act0) o[0] = y0;
-                if (act1) o[1] = y1;
+                if (act0) o[0] = y.x;
+                if (act1) o[1] = y.y;
             }
         }
     }
