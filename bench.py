@@ -906,7 +906,8 @@ def run_profile_workload(name):
     """A small case of one row, run twice, for ncu captures (a few hundred MB on the device):
     taylor = fcc 32^3, 321^3 voxels, P = 12 (taylor30: P = 30, 5456 monomials); fft64 = the perovskite 64^3 model at P = 4 (175 fields
     of 64^3), |hkl| <= 2; lanczos = occupancy 32^3 cells, 513^3 voxels,
-    m = 2, m' = 8; subbox = the pyrochlore occupancy volume with n_sb = 5; subbox_dft = the
+    m = 2, m' = 8 (lanczos1025: the full 64^3-cell, 1025^3-voxel row, about 13 GB on the device:
+    for one-pass launch lists only); subbox = the pyrochlore occupancy volume with n_sb = 5; subbox_dft = the
     random-origin displacive boxes on a 101 x 101 (h h l) plane; dw = the magnetic pyrochlore
     with T_mu(G), |hkl| <= 1."""
     import ctypes
@@ -929,8 +930,8 @@ def run_profile_workload(name):
         lm = ds.Model(ctx, m.lattice, m.sites, m.cells, 1, m.scat_len, m.ff_kind, m.ff_coef)
         lm.upload_displacements(np.ascontiguousarray(m.disp))
         opts = dict(disorder=ds.DS_DISP, mode=ds.DS_TOTAL, precision=ds.DS_FP32, taylor_order=4)
-    elif name == "lanczos":
-        n = 32
+    elif name in ("lanczos", "lanczos1025"):
+        n = 64 if name == "lanczos1025" else 32
         m = syn.Model(lattice=(4.0, 4.0, 4.0, 90.0, 90.0, 90.0), sites=np.array([[0.0, 0.0, 0.0]]),
                       scat_len=np.ones(1), ff_kind=np.zeros(1, dtype=np.int32), ff_coef=np.zeros((1, 9)),
                       cells=(n, n, n), nmodels=1)
@@ -1125,7 +1126,7 @@ def main():
     ap.add_argument("--serving", type=int, default=512, help="requests in the serving stream (0 = skip)")
     ap.add_argument("--no-rows", action="store_true", help="skip the per-row measurements")
     ap.add_argument("--no-graph", action="store_true", help="time direct calls instead of a replayed CUDA graph")
-    ap.add_argument("--profile-workload", choices=["taylor", "taylor30", "fft64", "lanczos", "subbox", "subbox_dft", "dw"], default=None,
+    ap.add_argument("--profile-workload", choices=["taylor", "taylor30", "fft64", "lanczos", "lanczos1025", "subbox", "subbox_dft", "dw"], default=None,
                     help="run one small row workload twice (for ncu captures) and exit")
     ap.add_argument("--streams", type=int, default=2, choices=[1, 2],
                     help="2: the two volumes of a step on two streams (their kernels overlap)")
