@@ -516,53 +516,68 @@ __global__ void __launch_bounds__(256) k_fft_planes64(const FieldSource src, int
     }
 }
 
-// Axis 1 of 32 columns (k2, k3) of one field's work planes: the 64 x 32 block is read with
-// coalesced rows, transformed by eight threads per column, and the half spectrum written with
-// coalesced rows (times i^n for Taylor monomials).
+// Axis 1 of 32 columns (k2, k3) of one field's work planes per block: the 64 x 32 block is staged
+// in shared memory, transformed by eight threads per column, and the half spectrum written with
+// coalesced rows (times i^n for Taylor monomials).  Persistent CTAs (as many as fit at once) take
+// the blocks round-robin and copy the next block asynchronously into a second buffer while the
+// current one is transformed, so the block loads stay in flight behind the arithmetic.
+constexpr int C64_THREADS = 256;
 template <typename T>
-__global__ void __launch_bounds__(256) k_fft_columns64(const FieldSource src, int f0, const c_t<T> *work,
-                                                       c_t<T> *spec) {
+__global__ void __launch_bounds__(C64_THREADS) k_fft_columns64(const FieldSource src, int f0, int nf,
+                                                               const c_t<T> *work, c_t<T> *spec) {
     using C = c_t<T>;
     constexpr int N = 64, NCOL = 64 * 33, CB = 32, CS = CB + 1, NCH = NCOL / CB;
     griddep_launch_dependents();   // the consumer of the spectra may be scheduled
     __shared__ __align__(16) C tr[8][4][F64_LS];
-    __shared__ __align__(16) C cb[N * CS];
+    extern __shared__ __align__(16) unsigned char c64_raw[];   // two blocks of N x CS values
+    C(*cb)[N * CS] = (C(*)[N * CS])c64_raw;
     const int tid = threadIdx.x, warp = tid >> 5, lw = (tid >> 3) & 3, t = tid & 7;
     const int line = warp * 4 + lw;
     C *area = &tr[warp][lw][0];
     C tw[8];
     fft64_twiddles<T>(t, tw);
-    const int fl = blockIdx.x / NCH, c0 = (blockIdx.x - fl * NCH) * CB, f = f0 + fl;
-    const C *in = work + (size_t)fl * N * NCOL + c0;
-    {
-        // the block's 2048 values, eight loads in flight per thread
-        C x[N * CB / 256];
+    const long long nblk = (long long)nf * NCH;
+    // block b: field b / NCH, columns (b mod NCH) CB .. + CB - 1, 2048 values, eight copies per thread
+    auto fetch = [&](long long b, int buf) {
+        const int fl = (int)(b / NCH), c0 = (int)(b - (long long)fl * NCH) * CB;
+        const C *in = work + (size_t)fl * N * NCOL + c0;
 #pragma unroll
-        for (int u = 0; u < N * CB / 256; ++u) {
-            const int i = tid + 256 * u, r = i >> 5, c = i & (CB - 1);
-            x[u] = in[(size_t)r * NCOL + c];
+        for (int u = 0; u < N * CB / C64_THREADS; ++u) {
+            const int i = tid + C64_THREADS * u, r = i >> 5, c = i & (CB - 1);
+            cp_async<sizeof(C)>(&cb[buf][r * CS + c], in + (size_t)r * NCOL + c);
         }
-#pragma unroll
-        for (int u = 0; u < N * CB / 256; ++u) {
-            const int i = tid + 256 * u, r = i >> 5, c = i & (CB - 1);
-            cb[r * CS + c] = x[u];
+        cp_async_commit();
+    };
+    long long b = blockIdx.x;
+    if (b < nblk) fetch(b, 0);
+    for (int it = 0; b < nblk; ++it, b += gridDim.x) {
+        const int cur = it & 1;
+        const long long bn = b + gridDim.x;
+        if (bn < nblk) {
+            fetch(bn, cur ^ 1);
+            cp_async_wait<1>();   // this block's copies have landed (the next block's may not)
+        } else {
+            cp_async_wait<0>();
         }
-    }
-    __syncthreads();
-    C v[8];
+        __syncthreads();
+        C *blk = cb[cur];
+        C v[8];
 #pragma unroll
-    for (int m = 0; m < 8; ++m) v[m] = cb[(t + 8 * m) * CS + line];
-    fft64_line<T>(v, tw, area, t);
+        for (int m = 0; m < 8; ++m) v[m] = blk[(t + 8 * m) * CS + line];
+        fft64_line<T>(v, tw, area, t);
 #pragma unroll
-    for (int k2 = 0; k2 < 8; ++k2) cb[(t + 8 * k2) * CS + line] = v[k2];
-    __syncthreads();
-    int rot = 0;
-    if (src.kind == SRC_DISP) rot = src.terms[(f % src.nf_per_model) % src.T].w;
-    C *out = spec + (size_t)f * (N * NCOL) + c0;
+        for (int k2 = 0; k2 < 8; ++k2) blk[(t + 8 * k2) * CS + line] = v[k2];
+        __syncthreads();
+        const int fl = (int)(b / NCH), c0 = (int)(b - (long long)fl * NCH) * CB, f = f0 + fl;
+        int rot = 0;
+        if (src.kind == SRC_DISP) rot = src.terms[(f % src.nf_per_model) % src.T].w;
+        C *out = spec + (size_t)f * (N * NCOL) + c0;
 #pragma unroll
-    for (int i = tid; i < N * CB; i += 256) {
-        const int k1 = i >> 5, c = i & (CB - 1);
-        out[(size_t)k1 * NCOL + c] = cipow(cb[k1 * CS + c], rot);
+        for (int i = tid; i < N * CB; i += C64_THREADS) {
+            const int k1 = i >> 5, c = i & (CB - 1);
+            out[(size_t)k1 * NCOL + c] = cipow(blk[k1 * CS + c], rot);
+        }
+        __syncthreads();   // the buffer is free for the copies of the block after next
     }
 }
 
@@ -574,7 +589,19 @@ static bool fft_lines64(const Geometry &g, const FieldSource &src, int f0, int n
     } else {
         if (g.n[0] != 64 || g.n[1] != 64 || g.n[2] != 64 || (size_t)nf * 64 >= (1u << 31)) return false;
         k_fft_planes64<T><<<(unsigned)(nf * 64), 256, 0, s>>>(src, f0, work);
-        k_fft_columns64<T><<<(unsigned)(nf * 66), 256, 0, s>>>(src, f0, work, spec);
+        constexpr size_t sm = 2 * 64 * 33 * sizeof(c_t<T>);   // the two block buffers
+        static thread_local int c_dev = -1, c_grid = 0;
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (dev != c_dev) {
+            int nsm = 0, per = 0;
+            cudaFuncSetAttribute(k_fft_columns64<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+            cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_fft_columns64<T>, C64_THREADS, sm);
+            c_dev = dev, c_grid = std::max(1, nsm * std::max(per, 1));
+        }
+        const long long nblk = (long long)nf * 66;
+        k_fft_columns64<T><<<(unsigned)std::min<long long>(nblk, c_grid), C64_THREADS, sm, s>>>(src, f0, nf, work, spec);
         count_launches(2);
         return true;
     }
