@@ -261,6 +261,38 @@ def test_points_errors(ctx):
     assert out.shape == (0,) and info["nvox"] == 0
 
 
+def test_points_checked_on_the_device(ctx):
+    """Points given on the device are scaled and bounded there: the first non-finite point is
+    reported by its index (here the 2nd of three in a block of 300, and again past the first
+    block of the reduction), points whose box of Bragg positions would be too long along an axis
+    are refused, and a valid device request matches the same request from host memory bit for
+    bit."""
+    import torch
+    import paper_1809_07088_gb300 as ds
+    m = syn.small_case(syn.OCC, cells=(3, 3, 3), nsite=1, nmodels=1, seed=134)
+    lm = to_library(ctx, m)
+    rng = np.random.default_rng(5)
+    for bad_at in (151, 1000):
+        hkl = rng.uniform(-1.0, 1.0, (1200, 3))
+        hkl[bad_at, 1] = np.inf
+        hkl[bad_at + 7, 0] = np.nan
+        with pytest.raises(ds.DSError) as e:
+            lm.intensity_points(torch.from_numpy(hkl).cuda(), out=torch.empty(1200, device="cuda"),
+                                disorder=0, precision=1)
+        assert "DS_ERR_ARG" in str(e.value) and ("point %d is not finite" % bad_at) in str(e.value)
+    far = np.array([[0.0, 0.0, 0.0], [0.0, 2.0e6, 0.0]])
+    with pytest.raises(ds.DSError) as e:
+        lm.intensity_points(torch.from_numpy(far).cuda(), out=torch.empty(2, device="cuda"), disorder=0,
+                            precision=1)
+    assert "DS_ERR_UNSUPPORTED" in str(e.value) and "axis 1" in str(e.value)
+    hkl = rng.uniform(-1.2, 1.1, (777, 3))
+    host, _ = lm.intensity_points(hkl, disorder=0, mode=1, precision=1)
+    dev = torch.empty(777, dtype=torch.float32, device="cuda")
+    lm.intensity_points(torch.from_numpy(hkl).cuda(), out=dev, disorder=0, mode=1, precision=1)
+    torch.cuda.synchronize()
+    assert np.array_equal(dev.cpu().numpy(), host)
+
+
 @pytest.mark.parametrize("prec,tag", PREC)
 @pytest.mark.parametrize("m_,mp", [(2, 2), (3, 2), (2, 4), (3, 3)])
 def test_sphere_cutoff_commensurate_and_points(ctx, prec, tag, m_, mp):
