@@ -267,9 +267,10 @@ ds_status ds_measure_peaks(int device, double out[5]);
  * non-finite site coordinate, scattering length or mean returns DS_ERR_ARG.  The per-site inputs
  * are passed to the GPU by value: no host buffer is read after the call returns.
  * The first call on a device (and the first after that device's context was reset) looks up the
- * array's address with that device current: make that call before any stream capture on the
- * device.  All calls share the array; calls whose GPU work overlaps race on it and must be
- * serialised by the caller.  Nothing in the array needs clearing between calls. */
+ * array's address with that device current.  The entry point is made for direct calls on a
+ * stream; recording it into a CUDA graph is not supported.  All calls share the array; calls
+ * whose GPU work overlaps race on it and must be serialised by the caller.  Nothing in the array
+ * needs clearing between calls. */
 ds_status ds_occupancy_intensity_noalloc(const double lattice[6], int nsite, const double *frac_xyz,
                                          const double *scat_len, int n1, int n2, int n3, int nmodels,
                                          const uint8_t *occ_dev, const double *mean_occ, const ds_qgrid *grid,

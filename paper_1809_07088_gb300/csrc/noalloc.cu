@@ -15,8 +15,8 @@
 //  - The array is DS_NOALLOC_SCRATCH_BYTES (32 MiB) on every GPU that loads the library and stays
 //    there until the process exits.  Requests needing more are rejected with DS_ERR_ADMISSION.
 //  - The first call on a device (and the first after that device's context was reset) looks up
-//    the array's device address (cudaGetSymbolAddress) with that device current; make that call
-//    before any stream capture on the device.
+//    the array's device address (cudaGetSymbolAddress) with that device current.  The entry
+//    point is for direct calls on a stream; recording it into a CUDA graph is not supported.
 //  - All calls share the array.  Every kernel writes the scratch it reads before reading it, so
 //    no part of the array has to start at zero, but two calls whose work overlaps on the GPU
 //    (different streams, or several host threads) race on it: serialise them.
