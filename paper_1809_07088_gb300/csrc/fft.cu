@@ -271,14 +271,18 @@ __global__ void __launch_bounds__(512) k_fft_field(Geometry g, FieldSource src, 
 // along axis 2 and axis 1 are transformed in registers; the axis-1 pass writes the half spectrum
 // [k1][k2][k3 <= N3/2] straight to HBM (coalesced across the CTA), times i^n for monomials.
 // One barrier per axis.
-constexpr int FR_THREADS = 512;
+// threads per CTA: at least one per row pair of axis 3 and one per line of axes 2 and 1; more
+// threads shorten the staging of the field values, which is bound by the latency of its loads
+// (20³ fields: 1024 threads stage in two rounds of loads instead of four)
+template <int N> constexpr int fr_threads() { return (N > 8 && N <= 20) ? 1024 : 512; }
 
 template <typename T, int N1, int N2, int N3>
-__global__ void __launch_bounds__(FR_THREADS, 1) k_fft_field_reg(const Geometry g, const FieldSource src, int f0,
+__global__ void __launch_bounds__(fr_threads<N1>(), 1) k_fft_field_reg(const Geometry g, const FieldSource src, int f0,
                                                               c_t<T> *spec) {
     using C = c_t<T>;
     constexpr int N3H = N3 / 2 + 1, NROW = N1 * N2, NPAIR = (NROW + 1) / 2, N3P = N3 + 1;
     constexpr int NCELL = N1 * N2 * N3;
+    constexpr int FR_THREADS = fr_threads<N1>();
     static_assert(NPAIR <= FR_THREADS, "one row pair per thread");
     griddep_launch_dependents();   // the consumer of the spectra may be scheduled
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -362,7 +366,7 @@ template <typename T, int N> static bool launch_field_reg(const Geometry &g, con
     constexpr size_t sm = (size_t)N * N * (N / 2 + 1) * sizeof(c_t<T>);
     if (sm > 48 * 1024)
         cudaFuncSetAttribute(k_fft_field_reg<T, N, N, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    k_fft_field_reg<T, N, N, N><<<(unsigned)nf, FR_THREADS, sm, s>>>(g, src, f0, spec);
+    k_fft_field_reg<T, N, N, N><<<(unsigned)nf, fr_threads<N>(), sm, s>>>(g, src, f0, spec);
     count_launches(1);
     return true;
 }
