@@ -293,9 +293,8 @@ __global__ void __launch_bounds__(fr_threads<N1>(), 1) k_fft_field_reg(const Geo
     // four consecutive cells per load (N3 % 4 == 0): 16-byte loads of the power rows, 4-byte loads
     // of the occupancies
     static_assert(N3 % 4 == 0, "rows of whole float4 groups");
-    for (int c4 = tid; c4 < NCELL / 4; c4 += FR_THREADS) {
-        const int c = 4 * c4, row = c / N3, r3 = c - row * N3;
-        T v[4];
+    // values of the four cells of group c4 (cells 4 c4 .. 4 c4 + 3)
+    auto load4 = [&](int c4, T (&v)[4]) {
         if (fr.kind == SRC_DISP) {
             const float4 a = ((const float4 *)fr.pw[0])[c4], b = ((const float4 *)fr.pw[1])[c4],
                          d = ((const float4 *)fr.pw[2])[c4];
@@ -309,10 +308,30 @@ __global__ void __launch_bounds__(fr_threads<N1>(), 1) k_fft_field_reg(const Geo
             v[0] = (T)o.x - fr.mean, v[1] = (T)o.y - fr.mean, v[2] = (T)o.z - fr.mean, v[3] = (T)o.w - fr.mean;
         } else {
 #pragma unroll
-            for (int q = 0; q < 4; ++q) v[q] = row_value<T>(fr, c + q);
+            for (int q = 0; q < 4; ++q) v[q] = row_value<T>(fr, 4 * c4 + q);
         }
+    };
+    auto store4 = [&](int c4, const T (&v)[4]) {
+        const int c = 4 * c4, row = c / N3, r3 = c - row * N3;
 #pragma unroll
         for (int q = 0; q < 4; ++q) val[row * N3P + r3 + q] = v[q];
+    };
+    constexpr int NG4 = NCELL / 4, NIT = (NG4 + FR_THREADS - 1) / FR_THREADS;
+    if constexpr (NIT <= 2) {
+        // every group of the thread loaded before any is stored: one round of load latency
+        T v[NIT][4];
+#pragma unroll
+        for (int u = 0; u < NIT; ++u)
+            if (tid + u * FR_THREADS < NG4) load4(tid + u * FR_THREADS, v[u]);
+#pragma unroll
+        for (int u = 0; u < NIT; ++u)
+            if (tid + u * FR_THREADS < NG4) store4(tid + u * FR_THREADS, v[u]);
+    } else {
+        for (int c4 = tid; c4 < NG4; c4 += FR_THREADS) {
+            T v[4];
+            load4(c4, v);
+            store4(c4, v);
+        }
     }
     __syncthreads();
     // axis 3: rows t and t + NPAIR as the real and imaginary parts of one line
