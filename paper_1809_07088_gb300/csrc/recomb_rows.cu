@@ -96,7 +96,8 @@ template <typename T> __device__ __forceinline__ typename Pair<T>::t pmk(T a, T 
 
 // shared-memory layout (byte offsets, 16-byte aligned).  PW: per site and class (rho2, rho3) the
 // phase w as (w.x, w.x, -w.y, w.y) in FP32 (the two FFMA2 multiplicands), w itself in FP64; YS: per
-// site, component and k3 the weighted transform y as (y.x, y.y, y.y, y.x) in FP32, y in FP64
+// site, component and k3 the weighted transform y (8 bytes in FP32: the swapped pair (y.y, y.x) the
+// second FFMA2 needs is formed in registers, once per load and reused over the classes)
 struct RowsLayout {
     size_t PW, YS, tab, rq, re, ro, mo, total;
 };
@@ -106,7 +107,7 @@ __host__ __device__ __forceinline__ RowsLayout rows_layout(int nsite, int nc, in
     RowsLayout L;
     L.PW = 0;
     L.YS = al(L.PW + (size_t)nsite * d2 * d3 * 16);
-    L.tab = al(L.YS + (size_t)nsite * nc * n3 * 16);
+    L.tab = al(L.YS + (size_t)nsite * nc * n3 * 2 * te);
     L.rq = al(L.tab + (size_t)d2 * d3 * n3 * tw * te);
     L.re = al(L.rq + (size_t)2 * RW_ROWS * 4 * te);
     L.ro = al(L.re + (size_t)2 * RW_ROWS * RW_MAXNG * te);
@@ -116,9 +117,9 @@ __host__ __device__ __forceinline__ RowsLayout rows_layout(int nsite, int nc, in
 }
 
 // acc += w y for complex w, y: FP32 from the packed forms (two FFMA2), FP64 directly
-__device__ __forceinline__ void tab_fma(float2 &acc, const float4 &w, const float4 &y) {
-    acc = __ffma2_rn(make_float2(w.x, w.y), make_float2(y.x, y.y), acc);
-    acc = __ffma2_rn(make_float2(w.z, w.w), make_float2(y.z, y.w), acc);
+__device__ __forceinline__ void tab_fma(float2 &acc, const float4 &w, const float2 &y) {
+    acc = __ffma2_rn(make_float2(w.x, w.y), y, acc);
+    acc = __ffma2_rn(make_float2(w.z, w.w), make_float2(y.y, y.x), acc);
 }
 __device__ __forceinline__ void tab_fma(double2 &acc, const double2 &w, const double2 &y) {
     acc.x = fma(w.x, y.x, fma(-w.y, y.y, acc.x));
@@ -128,12 +129,14 @@ template <typename T> struct Packed;
 template <> struct Packed<float> {
     using t = float4;
     static __device__ __forceinline__ float4 phase(float2 w) { return make_float4(w.x, w.x, -w.y, w.y); }
-    static __device__ __forceinline__ float4 value(float2 y) { return make_float4(y.x, y.y, y.y, y.x); }
+    using y = float2;
+    static __device__ __forceinline__ float2 value(float2 v) { return v; }
 };
 template <> struct Packed<double> {
     using t = double2;
     static __device__ __forceinline__ double2 phase(double2 w) { return w; }
-    static __device__ __forceinline__ double2 value(double2 y) { return y; }
+    using y = double2;
+    static __device__ __forceinline__ double2 value(double2 v) { return v; }
 };
 
 }  // namespace
@@ -178,7 +181,8 @@ __global__ void __launch_bounds__(RW_THREADS, sizeof(T) == 4 ? 6 : 3)
     const int nsite = p.nsite, d23 = d2 * d3;
     const RowsLayout L = rows_layout(nsite, NC, n3, d2, d3, sizeof(T));
     PT *PW = (PT *)(smem + L.PW);
-    PT *YS = (PT *)(smem + L.YS);
+    using YT = typename PK::y;
+    YT *YS = (YT *)(smem + L.YS);
     T *tab = (T *)(smem + L.tab);
     T *rq = (T *)(smem + L.rq);
     T *re = (T *)(smem + L.re);
@@ -268,7 +272,7 @@ __global__ void __launch_bounds__(RW_THREADS, sizeof(T) == 4 ? 6 : 3)
                 for (int c = 0; c < NC; ++c) F[i][c] = pmk<T>(T(0), T(0));
             }
             for (int sp = 0; sp < nsite; ++sp) {
-                PT y[NC];
+                YT y[NC];
 #pragma unroll
                 for (int c = 0; c < NC; ++c) y[c] = YS[(sp * NC + c) * n3 + q3];
 #pragma unroll
